@@ -1,0 +1,164 @@
+// Internal state of a voxcap handle.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace vc {
+
+// A device allocation owned by the handle.
+template <typename T> struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  int alloc(size_t count);
+  void release();
+  ~DBuf() { release(); }
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+};
+
+template <typename T> int DBuf<T>::alloc(size_t count) {
+  if (count <= n && p) return VOXCAP_OK;
+  release();
+  if (count == 0) return VOXCAP_OK;
+  cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    p = nullptr;
+    (void)cudaGetLastError();
+    set_error("device allocation of " + std::to_string(count * sizeof(T)) + " bytes failed");
+    return VOXCAP_ERR_OOM;
+  }
+  n = count;
+  return VOXCAP_OK;
+}
+template <typename T> void DBuf<T>::release() {
+  if (p) cudaFree(p);
+  p = nullptr;
+  n = 0;
+}
+
+// Grid geometry shared by all structures of a handle.
+struct Geom {
+  int nx, ny, nz;      // voxels
+  int Lx, Ly, Lz;      // common face box (N+1 per axis)
+  int Mx, My, Mz;      // padded FFT lengths (>= 2N+1, even)
+  int Hx;              // Mx/2 + 1
+  int Oy, Oz;          // My/2 + 1, Mz/2 + 1 (octant extents of the spectra)
+  __host__ __device__ int64_t box() const { return (int64_t)Lx * Ly * Lz; }
+};
+
+// The 15 kernel tensors: 0..5 P xx,yy,zz,xy,xz,yz ; 6..14 E xx,yy,zz,xy,xz,yz,yx,zx,zy
+constexpr int kNumKernels = 15;
+// test / source orientation of each kernel tensor
+__host__ __device__ __forceinline__ int ker_test(int kk) {
+  switch (kk) {
+    case 0: case 3: case 4: case 6: case 9: case 10: return 0;
+    case 1: case 5: case 7: case 11: case 12: return 1;
+    default: return 2;
+  }
+}
+__host__ __device__ __forceinline__ int ker_src(int kk) {
+  switch (kk) {
+    case 0: case 6: case 12: case 13: return 0;
+    case 1: case 3: case 7: case 9: case 14: return 1;
+    default: return 2;
+  }
+}
+
+struct Panels {
+  int S = 0;                      // structures
+  int64_t N = 0;                  // total panels
+  std::vector<int64_t> off, nc, nd;   // per structure
+  std::vector<int> m;             // conductors per structure
+  int m_max = 0;
+  DBuf<int8_t> orient, kind;
+  DBuf<int32_t> face;
+  DBuf<int16_t> owner;
+  DBuf<double> idiag, qscale;     // I' (Eq. 7), free-charge factor
+  DBuf<float> idiag_f;
+  DBuf<int32_t> la, lb;           // labels of the two sides (-1 outside)
+  DBuf<int32_t> fmap;             // [S][3][Lz][Ly][Lx] -> global panel index or -1
+  DBuf<int32_t> struct_of;        // [N] structure of each panel
+};
+
+struct Precond {
+  int kind = VOXCAP_PRECOND_BDD;
+  int nv[3] = {10, 10, 10};
+  int nbx = 0, nby = 0, nbz = 0;
+  int64_t nboxes = 0;             // (per structure) * S
+  int64_t nblocks = 0;            // non-empty boxes
+  int64_t nunique = 0;
+  int max_n = 0;
+  DBuf<int32_t> blk_off;          // [nblocks+1] offsets into blk_idx
+  DBuf<int32_t> blk_idx;          // panel indices, canonical order inside a block
+  DBuf<int32_t> blk_uid;          // [nblocks] unique-block id
+  DBuf<int64_t> uoff;             // [nunique+1] offsets (elements) of inverse matrices
+  DBuf<double> inv_d;             // unique inverses, row-major n x n each
+  DBuf<float> inv_f;
+  DBuf<double> dscale_d;          // per-panel diagonal factor for rows outside blocks (0 inside)
+  DBuf<float> dscale_f;
+};
+
+struct Handle {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  voxcap_opts opts;
+  double dv = 1.0;
+  int nlab = 0;
+  std::vector<int32_t> cid;
+  std::vector<double> eps;
+  DBuf<int32_t> labels;           // [S][nz][ny][nx]
+  DBuf<int32_t> cid_d;
+  DBuf<double> eps_d;
+  Geom g;
+  Panels pan;
+  Precond pre;
+  // FFT plans (twiddles owned here)
+  DBuf<double2> twd[3];
+  DBuf<float2> twf[3];
+  Plan1D<double2> pd[3];
+  Plan1D<float2> pf[3];
+  DBuf<double2> phd[3];           // exp(+i pi k / M) per axis, k in [0, M)
+  DBuf<float2> phf[3];
+  // Toeplitz tensors (FP64) and spectra
+  int tdims[kNumKernels][3];
+  DBuf<double> toep[kNumKernels];
+  DBuf<double> spec_d;            // [15][Oz][Oy][Hx] real, scaled by 1/(Mx My Mz)
+  DBuf<float> spec_f;
+  // MVM workspace
+  int ws_batch = 0;
+  DBuf<char> ws;                  // raw workspace
+  // solver workspace and results
+  DBuf<double> rho;               // last capacitance charges N x m_max
+  DBuf<double> rhs;               // last capacitance RHS
+  bool have_rho = false;
+  DBuf<char> solver_ws;
+};
+
+// ---- module entry points (host side) ----
+int build_fft_plans(Handle& h);
+int build_panels(Handle& h);
+int build_toeplitz(Handle& h);
+int build_spectra(Handle& h);
+int build_precond(Handle& h);
+// y = A x (or A^T x) for `nrhs` columns of the handle's N panels.
+// field_out (optional, double only): face-grid fields [nrhs][3][box] written
+// for every face (E-part for forward, full adjoint output for adjoint).
+template <typename T>
+int mvm(Handle& h, const T* x, T* y, int nrhs, bool adjoint, T* field_out);
+template <typename T>
+int precond_apply(Handle& h, const T* r, T* z, int nrhs);
+int solve(Handle& h, const double* B, int nrhs, double tol, double* X, voxcap_stats* st,
+          bool adjoint);
+int capacitance(Handle& h, double tol, double* C_host, double* rho_dev, voxcap_stats* st);
+int capacitance_grad(Handle& h, const double* dLdC, double tol, double* grad_host,
+                     voxcap_stats* st);
+// entries evaluated on arbitrary (kind, orientations, centre difference)
+int entries_eval(int n, const int32_t* kind, const int32_t* to, const int32_t* so,
+                 const double* d, double* out, cudaStream_t st);
+
+}  // namespace vc

@@ -1,0 +1,507 @@
+// FFT-accelerated products with the system matrix (Eqs. 9-11) and its
+// transpose, in FP32 or FP64.
+//
+// Forward (y = A x): the charges of the panels of each orientation b are
+// scattered onto the b-face grid (zero elsewhere, never materialised beyond
+// one row), transformed along x, y, z to the padded size M (R2C along x),
+// multiplied by the 15 kernel spectra (6 potential + 9 field blocks, Eq. 12
+// folds the other three potential blocks), transformed back, and gathered:
+// a conductor row takes the potential C^a at its face, a dielectric row
+// takes I' x + D^a (Eqs. 4, 9-11).
+//
+// Passes (one kernel each):
+//   xfwd  gather panel values into face rows, R2C along x (two real rows per
+//         complex line), half-voxel phase on the x grid
+//   yfwd  C2C along y (zero-padded input), phase on the y grid
+//   zmac  C2C along z, phase on the z grid, spectral multiply-accumulate,
+//         output phase on z outputs, inverse along z, truncation to N+1 planes
+//   yinv  inverse along y (truncated to N+1 rows), output phase on y outputs
+//   xinv  output phase on x outputs, C2R along x (two real rows per line),
+//         gather at the panels
+// The transposed product runs the same passes with the panel values split
+// by row kind (6 input grids), the conjugated kernels and 3 output grids.
+#include "internal.h"
+
+namespace vc {
+
+__constant__ int c_sig_y[kNumKernels];
+__constant__ int c_sig_z[kNumKernels];
+
+// fold sign of kernel kk along axis a: R(M-k) = sig * R(k)
+static int fold_sign(int kk, int a) {
+  const int te = ker_test(kk), so = ker_src(kk);
+  const bool E = kk >= 6;
+  if (te == so) return (E && a == te) ? -1 : 1;
+  if (a == te) return E ? 1 : -1;
+  if (a == so) return -1;
+  return 1;
+}
+
+static int ensure_sign_tables() {
+  int dev = 0;
+  VC_CUDA(cudaGetDevice(&dev));
+  static bool done[64] = {false};
+  if (dev < 64 && done[dev]) return VOXCAP_OK;
+  int sy[kNumKernels], sz[kNumKernels];
+  for (int kk = 0; kk < kNumKernels; ++kk) { sy[kk] = fold_sign(kk, 1); sz[kk] = fold_sign(kk, 2); }
+  VC_CUDA(cudaMemcpyToSymbol(c_sig_y, sy, sizeof(sy)));
+  VC_CUDA(cudaMemcpyToSymbol(c_sig_z, sz, sizeof(sz)));
+  if (dev < 64) done[dev] = true;
+  return VOXCAP_OK;
+}
+
+// index of the potential block of an unordered orientation pair, and of the
+// field block of an ordered (test, source) pair
+__device__ __forceinline__ int pidx(int a, int b) {
+  if (a == b) return a;
+  int lo = a < b ? a : b, hi = a < b ? b : a;
+  return lo == 0 ? (hi == 1 ? 3 : 4) : 5;
+}
+__device__ __forceinline__ int eidx(int a, int b) {
+  if (a == b) return 6 + a;
+  if (a == 0) return b == 1 ? 9 : 10;
+  if (a == 1) return b == 2 ? 11 : 12;
+  return b == 0 ? 13 : 14;
+}
+
+struct MvmArgs {
+  Geom g;
+  int nrhs;
+  int64_t N;
+  const int32_t* fmap;
+  const int8_t* kind;
+  const double* idiag;
+  const float* idiag_f;
+};
+
+template <typename T> __device__ __forceinline__ T idiag_of(const MvmArgs& a, int64_t p);
+template <> __device__ __forceinline__ float idiag_of<float>(const MvmArgs& a, int64_t p) { return a.idiag_f[p]; }
+template <> __device__ __forceinline__ double idiag_of<double>(const MvmArgs& a, int64_t p) { return a.idiag[p]; }
+
+// ------------------------------------------------------------------ xfwd
+// Forward: line l = rows (2l, 2l+1) of grid g.  Adjoint: line l = row l of
+// the conductor-source grid g (real part) and dielectric-source grid g (imag).
+template <typename T, bool ADJ>
+__global__ void k_xfwd(MvmArgs a, const T* __restrict__ xin, C_t<T>* __restrict__ out,
+                       Plan1D<C_t<T>> plan, const C_t<T>* __restrict__ phx, int NL) {
+  using C = C_t<T>;
+  extern __shared__ unsigned char smem_raw[];
+  const Geom& g = a.g;
+  const int M = g.Mx, H = g.Hx;
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  C* scr = buf + (size_t)M * NL;
+  const int z = blockIdx.y;
+  const int bg = blockIdx.z;             // b * 3 + grid
+  const int grid = bg % 3, b = bg / 3;
+  const int s = b / a.nrhs, r = b % a.nrhs;
+  const int nlines_total = ADJ ? g.Ly : (g.Ly + 1) / 2;
+  const int l0 = blockIdx.x * NL;
+  const int32_t* fm = a.fmap + (((int64_t)s * 3 + grid) * g.Lz + z) * ((int64_t)g.Ly * g.Lx);
+  const T* xr = xin + (int64_t)r * a.N;
+  for (int t = threadIdx.x; t < M * NL; t += blockDim.x) {
+    const int l = t % NL, x = t / NL;
+    T re = 0, im = 0;
+    const int line = l0 + l;
+    if (x < g.Lx && line < nlines_total) {
+      if (!ADJ) {
+        const int y0 = 2 * line, y1 = y0 + 1;
+        int p0 = fm[(int64_t)y0 * g.Lx + x];
+        if (p0 >= 0) re = xr[p0];
+        if (y1 < g.Ly) {
+          int p1 = fm[(int64_t)y1 * g.Lx + x];
+          if (p1 >= 0) im = xr[p1];
+        }
+      } else {
+        int p = fm[(int64_t)line * g.Lx + x];
+        if (p >= 0) {
+          if (a.kind[p] == 0) re = xr[p]; else im = xr[p];
+        }
+      }
+    }
+    buf[x * NL + l] = mk<C>(re, im);
+  }
+  __syncthreads();
+  C* res = fft_lines(buf, scr, NL, NL, plan, false);
+  const int GI = ADJ ? 6 : 3;
+  for (int t = threadIdx.x; t < H * NL; t += blockDim.x) {
+    const int l = t % NL, k = t / NL;
+    const int line = l0 + l;
+    if (line >= nlines_total) continue;
+    C zk = res[k * NL + l];
+    C zc = cconj(res[((M - k) % M) * NL + l]);
+    C A = cscale(cadd(zk, zc), (T)0.5);
+    C B = cscale(cmul_mi(csub(zk, zc)), (T)0.5);
+    if (grid == 0) { C ph = phx[k]; A = cmul(A, ph); B = cmul(B, ph); }
+    if (!ADJ) {
+      const int y0 = 2 * line, y1 = y0 + 1;
+      C* o = out + (((int64_t)b * GI + grid) * g.Lz + z) * ((int64_t)g.Ly * H);
+      o[(int64_t)y0 * H + k] = A;
+      if (y1 < g.Ly) o[(int64_t)y1 * H + k] = B;
+    } else {
+      C* oc = out + (((int64_t)b * GI + grid) * g.Lz + z) * ((int64_t)g.Ly * H);
+      C* od = out + (((int64_t)b * GI + 3 + grid) * g.Lz + z) * ((int64_t)g.Ly * H);
+      oc[(int64_t)line * H + k] = A;
+      od[(int64_t)line * H + k] = B;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ yfwd / yinv
+// in: [B][G][Lz][Lin][H] -> out: [B][G][Lz][Lout][H], transform along the
+// second-fastest axis.  Forward: Lin = Ly (zero-padded to My), Lout = My,
+// phase after.  Inverse: Lin = My, Lout = Ly (truncated), conj phase before.
+template <typename T, bool INV>
+__global__ void k_ypass(Geom g, int G, const C_t<T>* __restrict__ in, C_t<T>* __restrict__ out,
+                        Plan1D<C_t<T>> plan, const C_t<T>* __restrict__ phy, int TX) {
+  using C = C_t<T>;
+  extern __shared__ unsigned char smem_raw[];
+  const int M = g.My, H = g.Hx;
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  C* scr = buf + (size_t)M * TX;
+  const int k0 = blockIdx.x * TX;
+  const int z = blockIdx.y;
+  const int bg = blockIdx.z;           // b * G + grid
+  const int grid = bg % G;
+  const bool phase = (grid % 3) == 1;
+  const int Lin = INV ? M : g.Ly;
+  const int Lout = INV ? g.Ly : M;
+  const C* src = in + ((int64_t)bg * g.Lz + z) * ((int64_t)Lin * H);
+  C* dst = out + ((int64_t)bg * g.Lz + z) * ((int64_t)Lout * H);
+  for (int t = threadIdx.x; t < M * TX; t += blockDim.x) {
+    const int c = t % TX, y = t / TX;
+    const int kx = k0 + c;
+    C v = mk<C>((T)0, (T)0);
+    if (kx < H && y < Lin) {
+      v = src[(int64_t)y * H + kx];
+      if (INV && phase) v = cmul(v, cconj(phy[y]));
+    }
+    buf[y * TX + c] = v;
+  }
+  __syncthreads();
+  C* res = fft_lines(buf, scr, TX, TX, plan, INV);
+  for (int t = threadIdx.x; t < Lout * TX; t += blockDim.x) {
+    const int c = t % TX, y = t / TX;
+    const int kx = k0 + c;
+    if (kx >= H) continue;
+    C v = res[y * TX + c];
+    if (!INV && phase) v = cmul(v, phy[y]);
+    dst[(int64_t)y * H + kx] = v;
+  }
+}
+
+// ------------------------------------------------------------------ zmac
+// data: [B][6][Lz][My][H] (in place).  Forward reads grids 0..2, writes 0..5
+// (potential x,y,z then field x,y,z).  Adjoint reads 0..5 (conductor-source
+// x,y,z then dielectric-source x,y,z) and writes 0..2.
+template <typename T, bool ADJ>
+__global__ void k_zmac(Geom g, C_t<T>* __restrict__ data, const T* __restrict__ spec,
+                       Plan1D<C_t<T>> plan, const C_t<T>* __restrict__ phz, int TX) {
+  using C = C_t<T>;
+  extern __shared__ unsigned char smem_raw[];
+  constexpr int GI = ADJ ? 6 : 3;
+  constexpr int GO = ADJ ? 3 : 6;
+  const int M = g.Mz, H = g.Hx;
+  C* bufA = reinterpret_cast<C*>(smem_raw);
+  C* bufB = bufA + (size_t)M * 6 * TX;
+  const int b = blockIdx.x;
+  const int k0 = blockIdx.y * TX;
+  const int ky = blockIdx.z;
+  const int64_t gstride = (int64_t)g.Lz * g.My * H;     // one grid of one batch item
+  C* base = data + (int64_t)b * 6 * gstride + (int64_t)ky * H;
+  const int LI = GI * TX;
+  for (int t = threadIdx.x; t < M * LI; t += blockDim.x) {
+    const int col = t % LI, z = t / LI;
+    const int grid = col / TX, c = col % TX;
+    const int kx = k0 + c;
+    C v = mk<C>((T)0, (T)0);
+    if (kx < H && z < g.Lz) v = base[grid * gstride + (int64_t)z * g.My * H + kx];
+    bufA[z * LI + col] = v;
+  }
+  __syncthreads();
+  C* res = fft_lines(bufA, bufB, LI, LI, plan, false);
+  C* outb = (res == bufA) ? bufB : bufA;
+  const int LO = GO * TX;
+  const int64_t Otot = (int64_t)H * g.Oy * g.Oz;
+  const bool fy = ky > g.My / 2;
+  const int kyf = fy ? g.My - ky : ky;
+  for (int t = threadIdx.x; t < M * TX; t += blockDim.x) {
+    const int c = t % TX, kz = t / TX;
+    const int kx = k0 + c;
+    C o[GO];
+#pragma unroll
+    for (int q = 0; q < GO; ++q) o[q] = mk<C>((T)0, (T)0);
+    if (kx < H) {
+      const bool fz = kz > M / 2;
+      const int kzf = fz ? M - kz : kz;
+      const int64_t idx = ((int64_t)kzf * g.Oy + kyf) * H + kx;
+      T R[kNumKernels];
+#pragma unroll
+      for (int kk = 0; kk < kNumKernels; ++kk) {
+        T v = spec[kk * Otot + idx];
+        int sg = (fy ? c_sig_y[kk] : 1) * (fz ? c_sig_z[kk] : 1);
+        R[kk] = sg < 0 ? -v : v;
+      }
+      const C ph = phz[kz];
+      C in[GI];
+#pragma unroll
+      for (int q = 0; q < GI; ++q) {
+        in[q] = res[kz * LI + q * TX + c];
+        if (q % 3 == 2) in[q] = cmul(in[q], ph);     // half-voxel shift of z grids
+      }
+      if (!ADJ) {
+#pragma unroll
+        for (int al = 0; al < 3; ++al) {
+          C pa = mk<C>((T)0, (T)0), ea = mk<C>((T)0, (T)0);
+#pragma unroll
+          for (int be = 0; be < 3; ++be) {
+            pa = cadd(pa, cscale(in[be], R[pidx(al, be)]));
+            ea = cadd(ea, cscale(in[be], R[eidx(al, be)]));
+          }
+          o[al] = pa;
+          o[3 + al] = cmul_mi(ea);
+        }
+      } else {
+#pragma unroll
+        for (int be = 0; be < 3; ++be) {
+          C acc = mk<C>((T)0, (T)0), ei = mk<C>((T)0, (T)0);
+#pragma unroll
+          for (int al = 0; al < 3; ++al) {
+            acc = cadd(acc, cscale(in[al], R[pidx(al, be)]));
+            ei = cadd(ei, cscale(in[3 + al], R[eidx(al, be)]));
+          }
+          o[be] = cadd(acc, cmul_pi(ei));
+        }
+      }
+      const C phc = cconj(ph);
+#pragma unroll
+      for (int q = 0; q < GO; ++q)
+        if (q % 3 == 2) o[q] = cmul(o[q], phc);
+    }
+#pragma unroll
+    for (int q = 0; q < GO; ++q) outb[kz * LO + q * TX + c] = o[q];
+  }
+  __syncthreads();
+  C* res2 = fft_lines(outb, res, LO, LO, plan, true);
+  for (int t = threadIdx.x; t < g.Lz * LO; t += blockDim.x) {
+    const int col = t % LO, z = t / LO;
+    const int grid = col / TX, c = col % TX;
+    const int kx = k0 + c;
+    if (kx < H) base[grid * gstride + (int64_t)z * g.My * H + kx] = res2[z * LO + col];
+  }
+}
+
+// ------------------------------------------------------------------ xinv
+// Forward: line = row y of output orientation a: potential row (grid a) and
+// field row (grid 3+a) -> gather.  Adjoint: line = rows (2l, 2l+1) of grid a.
+template <typename T, bool ADJ>
+__global__ void k_xinv(MvmArgs a, const C_t<T>* __restrict__ in, const T* __restrict__ xin,
+                       T* __restrict__ yout, T* __restrict__ field, Plan1D<C_t<T>> plan,
+                       const C_t<T>* __restrict__ phx, int NL) {
+  using C = C_t<T>;
+  extern __shared__ unsigned char smem_raw[];
+  const Geom& g = a.g;
+  const int M = g.Mx, H = g.Hx;
+  constexpr int GO = ADJ ? 3 : 6;
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  C* scr = buf + (size_t)M * NL;
+  const int z = blockIdx.y;
+  const int bo = blockIdx.z;            // b * 3 + orientation
+  const int al = bo % 3, b = bo / 3;
+  const int s = b / a.nrhs, r = b % a.nrhs;
+  const int nlines_total = ADJ ? (g.Ly + 1) / 2 : g.Ly;
+  const int l0 = blockIdx.x * NL;
+  const int64_t plane = (int64_t)g.Ly * H;
+  const C* srcA;
+  const C* srcB;
+  if (!ADJ) {
+    srcA = in + (((int64_t)b * GO + al) * g.Lz + z) * plane;
+    srcB = in + (((int64_t)b * GO + 3 + al) * g.Lz + z) * plane;
+  } else {
+    srcA = in + (((int64_t)b * GO + al) * g.Lz + z) * plane;
+    srcB = srcA;
+  }
+  for (int t = threadIdx.x; t < M * NL; t += blockDim.x) {
+    const int l = t % NL, k = t / NL;
+    const int line = l0 + l;
+    C v = mk<C>((T)0, (T)0);
+    if (line < nlines_total) {
+      const int kk = k <= M / 2 ? k : M - k;
+      int64_t ra, rb;
+      bool hasb = true;
+      if (!ADJ) { ra = (int64_t)line * H; rb = ra; }
+      else {
+        ra = (int64_t)(2 * line) * H;
+        rb = ra + H;
+        hasb = (2 * line + 1) < g.Ly;
+      }
+      C A = srcA[ra + kk];
+      C B = hasb ? srcB[rb + kk] : mk<C>((T)0, (T)0);
+      if (al == 0) { C ph = cconj(phx[kk]); A = cmul(A, ph); B = cmul(B, ph); }
+      if (k > M / 2) { A = cconj(A); B = cconj(B); }
+      v = cadd(A, cmul_pi(B));
+    }
+    buf[k * NL + l] = v;
+  }
+  __syncthreads();
+  C* res = fft_lines(buf, scr, NL, NL, plan, true);
+  const int32_t* fm = a.fmap + (((int64_t)s * 3 + al) * g.Lz + z) * ((int64_t)g.Ly * g.Lx);
+  const T* xr = xin + (int64_t)r * a.N;
+  T* yr = yout + (int64_t)r * a.N;
+  for (int t = threadIdx.x; t < g.Lx * NL; t += blockDim.x) {
+    const int l = t % NL, x = t / NL;
+    const int line = l0 + l;
+    if (line >= nlines_total) continue;
+    C v = res[x * NL + l];
+    if (!ADJ) {
+      const int y = line;
+      int p = fm[(int64_t)y * g.Lx + x];
+      if (p >= 0) {
+        if (a.kind[p] == 0) yr[p] = v.x;
+        else yr[p] = idiag_of<T>(a, p) * xr[p] + v.y;
+      }
+      if (field)
+        field[(((int64_t)b * 3 + al) * g.Lz + z) * ((int64_t)g.Ly * g.Lx) + (int64_t)y * g.Lx + x] = v.y;
+    } else {
+      for (int h2 = 0; h2 < 2; ++h2) {
+        const int y = 2 * line + h2;
+        if (y >= g.Ly) break;
+        const T val = h2 == 0 ? v.x : v.y;
+        int p = fm[(int64_t)y * g.Lx + x];
+        if (p >= 0) yr[p] = val + (a.kind[p] == 1 ? idiag_of<T>(a, p) * xr[p] : (T)0);
+        if (field)
+          field[(((int64_t)b * 3 + al) * g.Lz + z) * ((int64_t)g.Ly * g.Lx) + (int64_t)y * g.Lx + x] = val;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ driver
+template <typename T> static int smem_lines(int L, int cols_per_line, int maxl) {
+  const size_t budget = 100 * 1024;
+  int nl = (int)(budget / (2 * (size_t)L * cols_per_line * sizeof(C_t<T>)));
+  int p = 1;
+  while (p * 2 <= nl && p * 2 <= maxl) p *= 2;
+  return p;
+}
+
+template <typename T> static const Plan1D<C_t<T>>& plan_of(const Handle& h, int a);
+template <> const Plan1D<float2>& plan_of<float>(const Handle& h, int a) { return h.pf[a]; }
+template <> const Plan1D<double2>& plan_of<double>(const Handle& h, int a) { return h.pd[a]; }
+template <typename T> static const C_t<T>* phase_of(const Handle& h, int a);
+template <> const float2* phase_of<float>(const Handle& h, int a) { return h.phf[a].p; }
+template <> const double2* phase_of<double>(const Handle& h, int a) { return h.phd[a].p; }
+template <typename T> static const T* spec_of(const Handle& h);
+template <> const float* spec_of<float>(const Handle& h) { return h.spec_f.p; }
+template <> const double* spec_of<double>(const Handle& h) { return h.spec_d.p; }
+
+template <typename T, typename K>
+static int set_smem(K kernel, size_t bytes) {
+  VC_CHECK(bytes <= 227 * 1024, VOXCAP_ERR_UNSUPPORTED, "FFT tile does not fit in shared memory");
+  VC_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  return VOXCAP_OK;
+}
+
+template <typename T>
+int mvm(Handle& h, const T* x, T* y, int nrhs, bool adjoint, T* field_out) {
+  using C = C_t<T>;
+  VC_TRY(ensure_sign_tables());
+  const Geom& g = h.g;
+  const int B = h.pan.S * nrhs;
+  const int64_t gX = (int64_t)g.Lz * g.Ly * g.Hx;     // one grid, x-pass layout
+  const int64_t gY = (int64_t)g.Lz * g.My * g.Hx;     // one grid, y/z-pass layout
+  const size_t need = sizeof(C) * ((size_t)B * 6 * gX + (size_t)B * 6 * gY);
+  VC_TRY(h.ws.alloc(need));
+  C* bufX = reinterpret_cast<C*>(h.ws.p);
+  C* bufY = bufX + (size_t)B * 6 * gX;
+  MvmArgs a;
+  a.g = g;
+  a.nrhs = nrhs;
+  a.N = h.pan.N;
+  a.fmap = h.pan.fmap.p;
+  a.kind = h.pan.kind.p;
+  a.idiag = h.pan.idiag.p;
+  a.idiag_f = h.pan.idiag_f.p;
+  const int GI = adjoint ? 6 : 3, GO = adjoint ? 3 : 6;
+  const int TB = 256;
+  cudaStream_t st = h.stream;
+  // xfwd
+  {
+    const int NL = smem_lines<T>(g.Mx, 1, 16);
+    const int lines = adjoint ? g.Ly : (g.Ly + 1) / 2;
+    dim3 grid((lines + NL - 1) / NL, g.Lz, B * 3);
+    size_t sm = 2 * (size_t)g.Mx * NL * sizeof(C);
+    if (adjoint) {
+      VC_TRY(set_smem<T>(k_xfwd<T, true>, sm));
+      k_xfwd<T, true><<<grid, TB, sm, st>>>(a, x, bufX, plan_of<T>(h, 0), phase_of<T>(h, 0), NL); ::vc::note_launch();
+    } else {
+      VC_TRY(set_smem<T>(k_xfwd<T, false>, sm));
+      k_xfwd<T, false><<<grid, TB, sm, st>>>(a, x, bufX, plan_of<T>(h, 0), phase_of<T>(h, 0), NL); ::vc::note_launch();
+    }
+    VC_CUDA(cudaGetLastError());
+  }
+  // yfwd: bufX [B][GI] -> bufY [B][6] (first GI grids).  The per-item grid
+  // stride differs (6 grids allocated), so launch per batch item block.
+  const int TXy = smem_lines<T>(g.My, 1, 16);
+  {
+    size_t sm = 2 * (size_t)g.My * TXy * sizeof(C);
+    VC_TRY(set_smem<T>(k_ypass<T, false>, sm));
+    for (int b = 0; b < B; ++b) {
+      dim3 grid((g.Hx + TXy - 1) / TXy, g.Lz, GI);
+      k_ypass<T, false><<<grid, TB, sm, st>>>(g, GI, bufX + (size_t)b * GI * gX,
+                                              bufY + (size_t)b * 6 * gY, plan_of<T>(h, 1),
+                                              phase_of<T>(h, 1), TXy); ::vc::note_launch();
+    }
+    VC_CUDA(cudaGetLastError());
+  }
+  // zmac
+  {
+    const int TXz = smem_lines<T>(g.Mz, 6, 16);
+    size_t sm = 2 * (size_t)g.Mz * 6 * TXz * sizeof(C);
+    dim3 grid(B, (g.Hx + TXz - 1) / TXz, g.My);
+    if (adjoint) {
+      VC_TRY(set_smem<T>(k_zmac<T, true>, sm));
+      k_zmac<T, true><<<grid, TB, sm, st>>>(g, bufY, spec_of<T>(h), plan_of<T>(h, 2),
+                                            phase_of<T>(h, 2), TXz); ::vc::note_launch();
+    } else {
+      VC_TRY(set_smem<T>(k_zmac<T, false>, sm));
+      k_zmac<T, false><<<grid, TB, sm, st>>>(g, bufY, spec_of<T>(h), plan_of<T>(h, 2),
+                                             phase_of<T>(h, 2), TXz); ::vc::note_launch();
+    }
+    VC_CUDA(cudaGetLastError());
+  }
+  // yinv: bufY [B][6] (first GO grids) -> bufX [B][GO]
+  {
+    size_t sm = 2 * (size_t)g.My * TXy * sizeof(C);
+    VC_TRY(set_smem<T>(k_ypass<T, true>, sm));
+    for (int b = 0; b < B; ++b) {
+      dim3 grid((g.Hx + TXy - 1) / TXy, g.Lz, GO);
+      k_ypass<T, true><<<grid, TB, sm, st>>>(g, GO, bufY + (size_t)b * 6 * gY,
+                                             bufX + (size_t)b * GO * gX, plan_of<T>(h, 1),
+                                             phase_of<T>(h, 1), TXy); ::vc::note_launch();
+    }
+    VC_CUDA(cudaGetLastError());
+  }
+  // xinv + gather
+  {
+    const int NL = smem_lines<T>(g.Mx, 1, 16);
+    const int lines = adjoint ? (g.Ly + 1) / 2 : g.Ly;
+    dim3 grid((lines + NL - 1) / NL, g.Lz, B * 3);
+    size_t sm = 2 * (size_t)g.Mx * NL * sizeof(C);
+    if (adjoint) {
+      VC_TRY(set_smem<T>(k_xinv<T, true>, sm));
+      k_xinv<T, true><<<grid, TB, sm, st>>>(a, bufX, x, y, field_out, plan_of<T>(h, 0),
+                                            phase_of<T>(h, 0), NL); ::vc::note_launch();
+    } else {
+      VC_TRY(set_smem<T>(k_xinv<T, false>, sm));
+      k_xinv<T, false><<<grid, TB, sm, st>>>(a, bufX, x, y, field_out, plan_of<T>(h, 0),
+                                             phase_of<T>(h, 0), NL); ::vc::note_launch();
+    }
+    VC_CUDA(cudaGetLastError());
+  }
+  return VOXCAP_OK;
+}
+
+template int mvm<float>(Handle&, const float*, float*, int, bool, float*);
+template int mvm<double>(Handle&, const double*, double*, int, bool, double*);
+
+}  // namespace vc

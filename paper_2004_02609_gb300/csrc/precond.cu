@@ -1,0 +1,557 @@
+// Block-diagonal-diagonal preconditioner (Eq. 14, Sec. II.D) and the
+// comparison variants of Sec. III.A.
+//
+// The bounding box is split into small boxes of nv[0] x nv[1] x nv[2] voxels.
+// A face at index i along its own normal axis belongs to box
+// min(i / nv, n_boxes - 1) (the far boundary faces join the last box) and to
+// box j / nv along the other axes.  For the paper's preconditioner (BDD) the
+// block of a box holds the conductor panels it owns, with entries P' read
+// from the FP64 Toeplitz tensors; its inverse preconditions those conductor
+// rows, and dielectric rows are scaled by 1/I'.  Boxes whose panel pattern
+// (orientations and face offsets from the box corner) is identical have
+// identical blocks, so only one inverse per distinct pattern is stored
+// (Sec. II.D point (ii)).  BD uses all panels of a box (dielectric rows with
+// E' + I'), DIAG uses 1/A_kk and NONE the identity.
+#include <vector>
+
+#include "internal.h"
+
+namespace vc {
+
+struct BoxGeom {
+  int n[3], nv[3], nb[3];
+  int64_t nbox;      // boxes per structure
+  int Lx, Ly, Lz;
+};
+
+// Panels selected for blocks: BDD -> conductor panels only; BD -> all.
+__device__ __forceinline__ bool selected(int kind, int mode) {
+  return mode == VOXCAP_PRECOND_BD || kind == 0;
+}
+
+// face-index range [lo, hi) of box coordinate bc along axis a for orientation o
+__device__ __forceinline__ void box_range(const BoxGeom& bg, int o, int a, int bc, int* lo, int* hi) {
+  *lo = bc * bg.nv[a];
+  int h = (bc + 1) * bg.nv[a];
+  if (a == o) {
+    if (bc == bg.nb[a] - 1) h = bg.n[a] + 1;
+  } else if (h > bg.n[a]) {
+    h = bg.n[a];
+  }
+  *hi = h;
+}
+
+// Walk the faces of one box in canonical order (orientation, face index);
+// `fn(p, o, i, j, k)` is called for every selected panel, in order, by the
+// whole block cooperatively; returns the count.  Two phases: count, then fill.
+template <bool FILL>
+__device__ int walk_box(const BoxGeom& bg, int s, int64_t box, const int32_t* __restrict__ fmap,
+                        const int8_t* __restrict__ kind, int mode, int32_t* __restrict__ out) {
+  __shared__ int warp_tot[32];
+  __shared__ int base_sh;
+  const int bx = (int)(box % bg.nb[0]);
+  const int by = (int)((box / bg.nb[0]) % bg.nb[1]);
+  const int bz = (int)(box / ((int64_t)bg.nb[0] * bg.nb[1]));
+  const int bcs[3] = {bx, by, bz};
+  if (threadIdx.x == 0) base_sh = 0;
+  __syncthreads();
+  for (int o = 0; o < 3; ++o) {
+    int lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) box_range(bg, o, a, bcs[a], &lo[a], &hi[a]);
+    const int ex = hi[0] - lo[0], ey = hi[1] - lo[1], ez = hi[2] - lo[2];
+    const int cnt = (ex > 0 && ey > 0 && ez > 0) ? ex * ey * ez : 0;
+    const int32_t* fm = fmap + ((int64_t)s * 3 + o) * ((int64_t)bg.Lz * bg.Ly * bg.Lx);
+    for (int c0 = 0; c0 < cnt; c0 += blockDim.x) {
+      const int c = c0 + threadIdx.x;
+      int p = -1;
+      if (c < cnt) {
+        const int i = lo[0] + c % ex, j = lo[1] + (c / ex) % ey, k = lo[2] + c / (ex * ey);
+        p = fm[((int64_t)k * bg.Ly + j) * bg.Lx + i];
+        if (p >= 0 && !selected(kind[p], mode)) p = -1;
+      }
+      const int flag = p >= 0;
+      // block exclusive scan of flags
+      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+      int v = flag;
+      for (int d = 1; d < 32; d <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += t;
+      }
+      if (lane == 31) warp_tot[wid] = v;
+      __syncthreads();
+      if (wid == 0) {
+        int w = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
+        for (int d = 1; d < 32; d <<= 1) {
+          int t = __shfl_up_sync(0xffffffffu, w, d);
+          if (lane >= d) w += t;
+        }
+        warp_tot[lane] = w;
+      }
+      __syncthreads();
+      const int excl = v - flag + (wid > 0 ? warp_tot[wid - 1] : 0);
+      const int tot = warp_tot[(blockDim.x >> 5) - 1];
+      if (FILL && flag) out[base_sh + excl] = p;
+      __syncthreads();
+      if (threadIdx.x == 0) base_sh += tot;
+      __syncthreads();
+    }
+  }
+  return base_sh;
+}
+
+__global__ void k_box_count(BoxGeom bg, const int32_t* fmap, const int8_t* kind, int mode,
+                            int32_t* counts) {
+  const int64_t gb = blockIdx.x;          // s * nbox + box
+  const int s = (int)(gb / bg.nbox);
+  const int64_t box = gb % bg.nbox;
+  int n = walk_box<false>(bg, s, box, fmap, kind, mode, nullptr);
+  if (threadIdx.x == 0) counts[gb] = n;
+}
+
+__global__ void k_box_fill(BoxGeom bg, const int32_t* fmap, const int8_t* kind, int mode,
+                           const int32_t* offs, int32_t* idx) {
+  const int64_t gb = blockIdx.x;
+  const int s = (int)(gb / bg.nbox);
+  const int64_t box = gb % bg.nbox;
+  walk_box<true>(bg, s, box, fmap, kind, mode, idx + offs[gb]);
+}
+
+// local pattern key of panel p in box gb: orientation, offsets from the box corner, kind
+__device__ __forceinline__ uint64_t pat_key(const BoxGeom& bg, int64_t gb, int p,
+                                            const int8_t* orient, const int32_t* face,
+                                            const int8_t* kind, const double* idiag, int mode) {
+  const int64_t box = gb % bg.nbox;
+  const int bx = (int)(box % bg.nb[0]);
+  const int by = (int)((box / bg.nb[0]) % bg.nb[1]);
+  const int bz = (int)(box / ((int64_t)bg.nb[0] * bg.nb[1]));
+  const int o = orient[p];
+  int F[3] = {bg.n[0], bg.n[1], bg.n[2]};
+  F[o] += 1;
+  const int f = face[p];
+  const int i = f % F[0], j = (f / F[0]) % F[1], k = f / (F[0] * F[1]);
+  uint64_t key = (uint64_t)o;
+  key = key * 4099u + (uint64_t)(i - bx * bg.nv[0]);
+  key = key * 4099u + (uint64_t)(j - by * bg.nv[1]);
+  key = key * 4099u + (uint64_t)(k - bz * bg.nv[2]);
+  key = key * 3u + (uint64_t)kind[p];
+  if (mode == VOXCAP_PRECOND_BD && kind[p] == 1) {
+    unsigned long long bits = (unsigned long long)__double_as_longlong(idiag[p]);
+    key ^= bits * 0x9E3779B97F4A7C15ull;
+  }
+  return key;
+}
+
+__global__ void k_box_hash(BoxGeom bg, int64_t nboxes, const int32_t* offs, const int32_t* idx,
+                           const int8_t* orient, const int32_t* face, const int8_t* kind,
+                           const double* idiag, int mode, uint64_t* hash) {
+  int64_t gb = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gb >= nboxes) return;
+  uint64_t hsh = 1469598103934665603ull;
+  for (int q = offs[gb]; q < offs[gb + 1]; ++q) {
+    uint64_t k = pat_key(bg, gb, idx[q], orient, face, kind, idiag, mode);
+    hsh ^= k;
+    hsh *= 1099511628211ull;
+    hsh ^= hsh >> 29;
+  }
+  hash[gb] = hsh;
+}
+
+// representative = lowest-index box with the same pattern (exact comparison)
+__global__ void k_box_rep(BoxGeom bg, int64_t nboxes, const int32_t* offs, const int32_t* idx,
+                          const int8_t* orient, const int32_t* face, const int8_t* kind,
+                          const double* idiag, int mode, const uint64_t* hash, int32_t* rep,
+                          int32_t* is_rep) {
+  int64_t gb = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gb >= nboxes) return;
+  const int n = offs[gb + 1] - offs[gb];
+  int r = (int)gb;
+  if (n > 0) {
+    for (int64_t c = 0; c < gb; ++c) {
+      if (hash[c] != hash[gb] || offs[c + 1] - offs[c] != n) continue;
+      bool same = true;
+      for (int q = 0; q < n && same; ++q)
+        same = pat_key(bg, c, idx[offs[c] + q], orient, face, kind, idiag, mode) ==
+               pat_key(bg, gb, idx[offs[gb] + q], orient, face, kind, idiag, mode);
+      if (same) { r = (int)c; break; }
+    }
+  }
+  rep[gb] = r;
+  is_rep[gb] = (n > 0 && r == (int)gb) ? 1 : 0;
+}
+
+__global__ void k_box_uid(int64_t nboxes, const int32_t* rep, const int32_t* rep_scan,
+                          const int32_t* offs, int32_t* uid) {
+  int64_t gb = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gb >= nboxes) return;
+  uid[gb] = (offs[gb + 1] > offs[gb]) ? rep_scan[rep[gb]] : -1;
+}
+
+// ---- entry of A between two panels from the Toeplitz tensors ----
+struct ToepTabs {
+  const double* T[kNumKernels];
+  int d[kNumKernels][3];
+  int n[3];
+};
+
+__device__ __forceinline__ int tidx_p(int a, int b) {
+  if (a == b) return a;
+  int lo = a < b ? a : b, hi = a < b ? b : a;
+  return lo == 0 ? (hi == 1 ? 3 : 4) : 5;
+}
+__device__ __forceinline__ int tidx_e(int a, int b) {
+  if (a == b) return 6 + a;
+  if (a == 0) return b == 1 ? 9 : 10;
+  if (a == 1) return b == 2 ? 11 : 12;
+  return b == 0 ? 13 : 14;
+}
+
+// A_kl for test panel (ot, it[]) and source (os, is[]) (face-grid coordinates)
+__device__ double a_entry(const ToepTabs& tt, bool E, int ot, const int* it, int os, const int* is) {
+  int te = ot, so = os;
+  int d[3] = {it[0] - is[0], it[1] - is[1], it[2] - is[2]};
+  int kk;
+  if (!E) {
+    // P is symmetric: P^{ba}(d) = P^{ab}(-d); tables exist for a <= b
+    kk = tidx_p(te, so);
+    if (te > so) {
+      int t = te; te = so; so = t;
+      d[0] = -d[0]; d[1] = -d[1]; d[2] = -d[2];
+    }
+  } else {
+    kk = tidx_e(te, so);
+  }
+  double sg = 1.0;
+  int e[3];
+  for (int a = 0; a < 3; ++a) {
+    const int v = d[a];
+    if (te == so) {
+      e[a] = v < 0 ? -v : v;
+      if (E && a == te && v < 0) sg = -sg;
+    } else if (a == te) {
+      e[a] = v >= 1 ? v - 1 : -v;
+      if (E && v < 1) sg = -sg;
+    } else if (a == so) {
+      e[a] = v >= 0 ? v : -v - 1;
+    } else {
+      e[a] = v < 0 ? -v : v;
+    }
+  }
+  const int* dd = tt.d[kk];
+  return sg * tt.T[kk][(int64_t)e[0] + (int64_t)dd[0] * (e[1] + (int64_t)dd[1] * e[2])];
+}
+
+__device__ __forceinline__ void face_coords(const int* n, int o, int f, int* c) {
+  int F[3] = {n[0], n[1], n[2]};
+  F[o] += 1;
+  c[0] = f % F[0];
+  c[1] = (f / F[0]) % F[1];
+  c[2] = f / (F[0] * F[1]);
+}
+
+// assemble [A_B | I] (n x 2n, row-major) for one unique block
+__global__ void k_assemble(ToepTabs tt, const int32_t* urep, const int32_t* offs, const int32_t* idx,
+                           const int64_t* uoff, const int8_t* orient, const int32_t* face,
+                           const int8_t* kind, const double* idiag, double* aug) {
+  const int u = blockIdx.x;
+  const int gb = urep[u];
+  const int q0 = offs[gb];
+  const int n = offs[gb + 1] - q0;
+  double* Mx = aug + 2 * uoff[u];
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    const int i = t / n, j = t % n;
+    const int pk = idx[q0 + i], pl = idx[q0 + j];
+    int ck[3], cl[3];
+    face_coords(tt.n, orient[pk], face[pk], ck);
+    face_coords(tt.n, orient[pl], face[pl], cl);
+    const bool E = kind[pk] == 1;
+    double v = a_entry(tt, E, orient[pk], ck, orient[pl], cl);
+    if (E && i == j) v += idiag[pk];
+    Mx[(int64_t)i * 2 * n + j] = v;
+    Mx[(int64_t)i * 2 * n + n + j] = (i == j) ? 1.0 : 0.0;
+  }
+}
+
+// Gauss-Jordan with partial pivoting on [A | I] -> [I | A^-1]; one block per matrix.
+__global__ void k_gauss_jordan(const int32_t* urep, const int32_t* offs, const int64_t* uoff,
+                               double* aug, int* status) {
+  const int u = blockIdx.x;
+  const int gb = urep[u];
+  const int n = offs[gb + 1] - offs[gb];
+  const int w = 2 * n;
+  double* Mx = aug + 2 * uoff[u];
+  __shared__ double red_v[256];
+  __shared__ int red_i[256];
+  __shared__ int piv_sh;
+  for (int c = 0; c < n; ++c) {
+    // pivot search in column c, rows c..n-1
+    double best = -1.0;
+    int bi = c;
+    for (int r = c + threadIdx.x; r < n; r += blockDim.x) {
+      double v = fabs(Mx[(int64_t)r * w + c]);
+      if (v > best) { best = v; bi = r; }
+    }
+    red_v[threadIdx.x] = best;
+    red_i[threadIdx.x] = bi;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+      if (threadIdx.x < st) {
+        if (red_v[threadIdx.x + st] > red_v[threadIdx.x] ||
+            (red_v[threadIdx.x + st] == red_v[threadIdx.x] && red_i[threadIdx.x + st] < red_i[threadIdx.x])) {
+          red_v[threadIdx.x] = red_v[threadIdx.x + st];
+          red_i[threadIdx.x] = red_i[threadIdx.x + st];
+        }
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      piv_sh = red_i[0];
+      if (!(red_v[0] > 0.0)) atomicExch(status, 1);
+    }
+    __syncthreads();
+    const int pr = piv_sh;
+    if (pr != c)
+      for (int j = threadIdx.x; j < w; j += blockDim.x) {
+        double t = Mx[(int64_t)c * w + j];
+        Mx[(int64_t)c * w + j] = Mx[(int64_t)pr * w + j];
+        Mx[(int64_t)pr * w + j] = t;
+      }
+    __syncthreads();
+    const double inv = 1.0 / Mx[(int64_t)c * w + c];
+    __syncthreads();
+    for (int j = threadIdx.x; j < w; j += blockDim.x) Mx[(int64_t)c * w + j] *= inv;
+    __syncthreads();
+    for (int t = threadIdx.x; t < n * w; t += blockDim.x) {
+      const int r = t / w, j = t % w;
+      if (r == c || j == c) continue;
+      Mx[(int64_t)r * w + j] -= Mx[(int64_t)r * w + c] * Mx[(int64_t)c * w + j];
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < n; r += blockDim.x)
+      if (r != c) Mx[(int64_t)r * w + c] = 0.0;
+    __syncthreads();
+  }
+}
+
+__global__ void k_extract_inv(const int32_t* urep, const int32_t* offs, const int64_t* uoff,
+                              const double* aug, double* inv_d, float* inv_f) {
+  const int u = blockIdx.x;
+  const int gb = urep[u];
+  const int n = offs[gb + 1] - offs[gb];
+  const double* Mx = aug + 2 * uoff[u];
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    const int i = t / n, j = t % n;
+    double v = Mx[(int64_t)i * 2 * n + n + j];
+    inv_d[uoff[u] + t] = v;
+    inv_f[uoff[u] + t] = (float)v;
+  }
+}
+
+__global__ void k_diag_scale(int64_t N, int mode, const int8_t* kind, const double* idiag,
+                             double pself, const int32_t* inblk, double* dd, float* df) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  double v;
+  if (mode == VOXCAP_PRECOND_NONE) v = 1.0;
+  else if (mode == VOXCAP_PRECOND_DIAG) v = kind[p] == 0 ? 1.0 / pself : 1.0 / idiag[p];
+  else if (inblk && inblk[p]) v = 0.0;
+  else v = kind[p] == 1 ? 1.0 / idiag[p] : 1.0 / pself;
+  dd[p] = v;
+  df[p] = (float)v;
+}
+
+__global__ void k_mark_inblk(int64_t total, const int32_t* idx, int32_t* inblk) {
+  int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < total) inblk[idx[q]] = 1;
+}
+
+int build_precond(Handle& h) {
+  Precond& P = h.pre;
+  P.kind = h.opts.precond;
+  for (int a = 0; a < 3; ++a) P.nv[a] = h.opts.nv[a] > 0 ? h.opts.nv[a] : 10;
+  const Geom& g = h.g;
+  const int64_t N = h.pan.N;
+  const int S = h.pan.S;
+  VC_TRY(P.dscale_d.alloc((size_t)std::max<int64_t>(N, 1)));
+  VC_TRY(P.dscale_f.alloc((size_t)std::max<int64_t>(N, 1)));
+  // self term P'_kk (identical for every orientation)
+  double pself = 0.0;
+  VC_CUDA(cudaMemcpy(&pself, h.toep[0].p, sizeof(double), cudaMemcpyDeviceToHost));
+  const int TB = 256;
+  P.nblocks = 0;
+  P.nunique = 0;
+  P.max_n = 0;
+  if (P.kind == VOXCAP_PRECOND_NONE || P.kind == VOXCAP_PRECOND_DIAG || N == 0) {
+    k_diag_scale<<<(unsigned)((N + TB - 1) / TB), TB, 0, h.stream>>>(
+        N, P.kind, h.pan.kind.p, h.pan.idiag.p, pself, nullptr, P.dscale_d.p, P.dscale_f.p); ::vc::note_launch();
+    VC_CUDA(cudaGetLastError());
+    VC_CUDA(cudaStreamSynchronize(h.stream));
+    return VOXCAP_OK;
+  }
+  BoxGeom bg;
+  bg.n[0] = g.nx; bg.n[1] = g.ny; bg.n[2] = g.nz;
+  for (int a = 0; a < 3; ++a) {
+    bg.nv[a] = P.nv[a];
+    bg.nb[a] = (bg.n[a] + P.nv[a] - 1) / P.nv[a];
+  }
+  bg.nbox = (int64_t)bg.nb[0] * bg.nb[1] * bg.nb[2];
+  bg.Lx = g.Lx; bg.Ly = g.Ly; bg.Lz = g.Lz;
+  P.nbx = bg.nb[0]; P.nby = bg.nb[1]; P.nbz = bg.nb[2];
+  const int64_t nboxes = bg.nbox * S;
+  P.nboxes = nboxes;
+  P.nblocks = nboxes;
+  VC_TRY(P.blk_off.alloc((size_t)nboxes + 1));
+  DBuf<int32_t> tmp;
+  VC_TRY(tmp.alloc((size_t)scan_tmp_elems(nboxes + 1) + 8));
+  VC_CUDA(cudaMemsetAsync(P.blk_off.p, 0, sizeof(int32_t) * (nboxes + 1), h.stream));
+  k_box_count<<<(unsigned)nboxes, TB, 0, h.stream>>>(bg, h.pan.fmap.p, h.pan.kind.p, P.kind, P.blk_off.p); ::vc::note_launch();
+  VC_CUDA(cudaGetLastError());
+  // counts -> offsets (scan over nboxes+1 so that blk_off[nboxes] = total)
+  std::vector<int32_t> cnt_h(nboxes);
+  VC_CUDA(cudaMemcpyAsync(cnt_h.data(), P.blk_off.p, sizeof(int32_t) * nboxes, cudaMemcpyDeviceToHost, h.stream));
+  int64_t total = 0;
+  VC_TRY(exclusive_scan_i32(P.blk_off.p, nboxes + 1, tmp.p, &total, h.stream));
+  for (int64_t b = 0; b < nboxes; ++b) P.max_n = std::max(P.max_n, (int)cnt_h[b]);
+  VC_TRY(P.blk_idx.alloc((size_t)std::max<int64_t>(total, 1)));
+  k_box_fill<<<(unsigned)nboxes, TB, 0, h.stream>>>(bg, h.pan.fmap.p, h.pan.kind.p, P.kind, P.blk_off.p,
+                                                   P.blk_idx.p); ::vc::note_launch();
+  VC_CUDA(cudaGetLastError());
+  // dedup
+  DBuf<uint64_t> hash;
+  DBuf<int32_t> rep, isrep;
+  VC_TRY(hash.alloc((size_t)nboxes));
+  VC_TRY(rep.alloc((size_t)nboxes));
+  VC_TRY(isrep.alloc((size_t)nboxes + 1));
+  VC_CUDA(cudaMemsetAsync(isrep.p, 0, sizeof(int32_t) * (nboxes + 1), h.stream));
+  unsigned nbk = (unsigned)((nboxes + TB - 1) / TB);
+  k_box_hash<<<nbk, TB, 0, h.stream>>>(bg, nboxes, P.blk_off.p, P.blk_idx.p, h.pan.orient.p,
+                                       h.pan.face.p, h.pan.kind.p, h.pan.idiag.p, P.kind, hash.p); ::vc::note_launch();
+  k_box_rep<<<nbk, TB, 0, h.stream>>>(bg, nboxes, P.blk_off.p, P.blk_idx.p, h.pan.orient.p,
+                                      h.pan.face.p, h.pan.kind.p, h.pan.idiag.p, P.kind, hash.p,
+                                      rep.p, isrep.p); ::vc::note_launch();
+  VC_CUDA(cudaGetLastError());
+  // unique ids: scan of is_rep; copy representatives to the host to size the storage
+  std::vector<int32_t> isrep_h(nboxes);
+  VC_CUDA(cudaMemcpyAsync(isrep_h.data(), isrep.p, sizeof(int32_t) * nboxes, cudaMemcpyDeviceToHost, h.stream));
+  int64_t nuniq = 0;
+  VC_TRY(exclusive_scan_i32(isrep.p, nboxes + 1, tmp.p, &nuniq, h.stream));
+  VC_TRY(P.blk_uid.alloc((size_t)nboxes));
+  k_box_uid<<<nbk, TB, 0, h.stream>>>(nboxes, rep.p, isrep.p, P.blk_off.p, P.blk_uid.p); ::vc::note_launch();
+  VC_CUDA(cudaGetLastError());
+  P.nunique = nuniq;
+  std::vector<int32_t> urep_h;
+  std::vector<int64_t> uoff_h(1, 0);
+  for (int64_t b = 0; b < nboxes; ++b)
+    if (isrep_h[b]) {
+      urep_h.push_back((int32_t)b);
+      uoff_h.push_back(uoff_h.back() + (int64_t)cnt_h[b] * cnt_h[b]);
+    }
+  const int64_t inv_elems = uoff_h.back();
+  DBuf<int32_t> urep;
+  VC_TRY(urep.alloc(std::max<size_t>(urep_h.size(), 1)));
+  VC_TRY(P.uoff.alloc(uoff_h.size()));
+  VC_TRY(P.inv_d.alloc((size_t)std::max<int64_t>(inv_elems, 1)));
+  VC_TRY(P.inv_f.alloc((size_t)std::max<int64_t>(inv_elems, 1)));
+  VC_CUDA(cudaMemcpyAsync(urep.p, urep_h.data(), sizeof(int32_t) * urep_h.size(), cudaMemcpyHostToDevice, h.stream));
+  VC_CUDA(cudaMemcpyAsync(P.uoff.p, uoff_h.data(), sizeof(int64_t) * uoff_h.size(), cudaMemcpyHostToDevice, h.stream));
+  if (nuniq > 0) {
+    DBuf<double> aug;
+    DBuf<int> status;
+    VC_TRY(aug.alloc((size_t)(2 * inv_elems)));
+    VC_TRY(status.alloc(1));
+    VC_CUDA(cudaMemsetAsync(status.p, 0, sizeof(int), h.stream));
+    ToepTabs tt;
+    for (int kk = 0; kk < kNumKernels; ++kk) {
+      tt.T[kk] = h.toep[kk].p;
+      for (int a = 0; a < 3; ++a) tt.d[kk][a] = h.tdims[kk][a];
+    }
+    tt.n[0] = g.nx; tt.n[1] = g.ny; tt.n[2] = g.nz;
+    k_assemble<<<(unsigned)nuniq, TB, 0, h.stream>>>(tt, urep.p, P.blk_off.p, P.blk_idx.p, P.uoff.p,
+                                                     h.pan.orient.p, h.pan.face.p, h.pan.kind.p,
+                                                     h.pan.idiag.p, aug.p); ::vc::note_launch();
+    k_gauss_jordan<<<(unsigned)nuniq, TB, 0, h.stream>>>(urep.p, P.blk_off.p, P.uoff.p, aug.p, status.p); ::vc::note_launch();
+    k_extract_inv<<<(unsigned)nuniq, TB, 0, h.stream>>>(urep.p, P.blk_off.p, P.uoff.p, aug.p, P.inv_d.p,
+                                                        P.inv_f.p); ::vc::note_launch();
+    VC_CUDA(cudaGetLastError());
+    int st = 0;
+    VC_CUDA(cudaMemcpyAsync(&st, status.p, sizeof(int), cudaMemcpyDeviceToHost, h.stream));
+    VC_CUDA(cudaStreamSynchronize(h.stream));
+    VC_CHECK(st == 0, VOXCAP_ERR_ARG, "singular preconditioner block");
+  }
+  DBuf<int32_t> inblk;
+  VC_TRY(inblk.alloc((size_t)std::max<int64_t>(N, 1)));
+  VC_CUDA(cudaMemsetAsync(inblk.p, 0, sizeof(int32_t) * std::max<int64_t>(N, 1), h.stream));
+  if (total > 0)
+    k_mark_inblk<<<(unsigned)((total + TB - 1) / TB), TB, 0, h.stream>>>(total, P.blk_idx.p, inblk.p); ::vc::note_launch();
+  k_diag_scale<<<(unsigned)((N + TB - 1) / TB), TB, 0, h.stream>>>(
+      N, P.kind, h.pan.kind.p, h.pan.idiag.p, pself, inblk.p, P.dscale_d.p, P.dscale_f.p); ::vc::note_launch();
+  VC_CUDA(cudaGetLastError());
+  VC_CUDA(cudaStreamSynchronize(h.stream));
+  return VOXCAP_OK;
+}
+
+// ---------------------------------------------------------------- apply
+template <typename T>
+__global__ void k_pre_diag(int64_t N, int nrhs, const T* __restrict__ ds, const T* __restrict__ r,
+                           T* __restrict__ z) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N * nrhs) return;
+  z[t] = ds[t % N] * r[t];
+}
+
+template <typename T>
+__global__ void k_pre_blocks(int64_t N, const int32_t* __restrict__ offs, const int32_t* __restrict__ idx,
+                             const int32_t* __restrict__ uid, const int64_t* __restrict__ uoff,
+                             const T* __restrict__ inv, const T* __restrict__ r, T* __restrict__ z) {
+  extern __shared__ unsigned char smem_raw[];
+  T* rv = reinterpret_cast<T*>(smem_raw);
+  const int64_t gb = blockIdx.x;
+  const int rhs = blockIdx.y;
+  const int q0 = offs[gb];
+  const int n = offs[gb + 1] - q0;
+  if (n == 0) return;
+  const T* Minv = inv + uoff[uid[gb]];
+  const T* rr = r + (int64_t)rhs * N;
+  T* zz = z + (int64_t)rhs * N;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) rv[j] = rr[idx[q0 + j]];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = wid; i < n; i += nw) {
+    double acc = 0.0;
+    const T* row = Minv + (int64_t)i * n;
+    for (int j = lane; j < n; j += 32) acc += (double)row[j] * (double)rv[j];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) zz[idx[q0 + i]] = (T)acc;
+  }
+}
+
+template <typename T> static const T* dscale_of(const Handle& h);
+template <> const float* dscale_of<float>(const Handle& h) { return h.pre.dscale_f.p; }
+template <> const double* dscale_of<double>(const Handle& h) { return h.pre.dscale_d.p; }
+template <typename T> static const T* inv_of(const Handle& h);
+template <> const float* inv_of<float>(const Handle& h) { return h.pre.inv_f.p; }
+template <> const double* inv_of<double>(const Handle& h) { return h.pre.inv_d.p; }
+
+template <typename T>
+int precond_apply(Handle& h, const T* r, T* z, int nrhs) {
+  const int64_t N = h.pan.N;
+  const int TB = 256;
+  if (N == 0) return VOXCAP_OK;
+  k_pre_diag<T><<<(unsigned)((N * nrhs + TB - 1) / TB), TB, 0, h.stream>>>(N, nrhs, dscale_of<T>(h), r, z); ::vc::note_launch();
+  VC_CUDA(cudaGetLastError());
+  const Precond& P = h.pre;
+  if ((P.kind == VOXCAP_PRECOND_BDD || P.kind == VOXCAP_PRECOND_BD) && P.nblocks > 0 && P.max_n > 0) {
+    size_t sm = sizeof(T) * (size_t)P.max_n;
+    if (sm > 48 * 1024)
+      VC_CUDA(cudaFuncSetAttribute(k_pre_blocks<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    dim3 grid((unsigned)P.nblocks, nrhs);
+    k_pre_blocks<T><<<grid, TB, sm, h.stream>>>(N, P.blk_off.p, P.blk_idx.p, P.blk_uid.p, P.uoff.p,
+                                                inv_of<T>(h), r, z); ::vc::note_launch();
+    VC_CUDA(cudaGetLastError());
+  }
+  return VOXCAP_OK;
+}
+
+template int precond_apply<float>(Handle&, const float*, float*, int);
+template int precond_apply<double>(Handle&, const double*, double*, int);
+
+}  // namespace vc

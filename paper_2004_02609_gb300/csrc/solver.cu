@@ -1,0 +1,518 @@
+// Iterative solution (Sec. III: GMRES with restart 35) of the left-
+// preconditioned system R A x = R b (Eq. 14), batched over right-hand sides,
+// inside an FP64 iterative-refinement loop, and the capacitance matrix of
+// Eq. 8.
+//
+// Arnoldi: classical Gram-Schmidt applied twice (CGS2) -- two fused
+// dot/update sweeps over the Krylov basis per step instead of the j+1
+// sequential sweeps of modified Gram-Schmidt, with at least its
+// orthogonality.  Inner products and norms accumulate in FP64; the Hessenberg
+// matrix, Givens rotations and residual estimates are FP64; the basis is
+// stored in the inner solve's precision (FP32 for the refinement path).
+//
+// Refinement: r = b - A x in FP64 (FP64 product), inner GMRES on A d = r in
+// FP32 (or FP64 for the plain path), x += d, until ||b - A x|| <= tol ||b||
+// per column.
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "internal.h"
+
+namespace vc {
+
+constexpr int kDotTB = 256;
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (wid == 0) {
+    t = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  }
+  return t;   // valid in thread 0
+}
+
+// partial[col][i][chunk] = sum over the chunk of V_i[col] * w[col], i < nv
+// (optionally first w -= sum_i coef[col][i] V_i[col]); with nv == 0 and
+// self-norm, partial = ||w||^2 over the chunk.
+template <typename T>
+__global__ void k_gs_sweep(const T* __restrict__ V, T* __restrict__ w, int64_t N, int nrhs,
+                           int nv_update, const double* __restrict__ coef, int coef_ld,
+                           int nv_dot, bool self_norm, const int* __restrict__ active,
+                           int nchunks, double* __restrict__ partial, int part_ld) {
+  __shared__ double sh[32];
+  const int col = blockIdx.y;
+  const int chunk = blockIdx.x;
+  if (active && !active[col]) return;
+  const int64_t per = (N + nchunks - 1) / nchunks;
+  const int64_t lo = chunk * per, hi = min(N, lo + per);
+  T* wc = w + (int64_t)col * N;
+  const int64_t vstride = (int64_t)nrhs * N;
+  if (nv_update > 0) {
+    for (int64_t p = lo + threadIdx.x; p < hi; p += blockDim.x) {
+      double acc = (double)wc[p];
+      for (int i = 0; i < nv_update; ++i)
+        acc -= coef[(int64_t)col * coef_ld + i] * (double)V[i * vstride + (int64_t)col * N + p];
+      wc[p] = (T)acc;
+    }
+    __syncthreads();
+  }
+  const int nd = self_norm ? 1 : nv_dot;
+  for (int i = 0; i < nd; ++i) {
+    double acc = 0.0;
+    const T* vi = self_norm ? wc : V + i * vstride + (int64_t)col * N;
+    for (int64_t p = lo + threadIdx.x; p < hi; p += blockDim.x) acc += (double)vi[p] * (double)wc[p];
+    double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) partial[((int64_t)col * part_ld + i) * nchunks + chunk] = s;
+  }
+}
+
+// out[col][i] (+)= sum_chunk partial[col][i][chunk]
+__global__ void k_reduce_partial(const double* __restrict__ partial, int nchunks, int ni, int part_ld,
+                                 const int* __restrict__ active, double* __restrict__ out, int out_ld,
+                                 bool accumulate) {
+  __shared__ double sh[32];
+  const int col = blockIdx.y, i = blockIdx.x;
+  if (active && !active[col]) return;
+  double acc = 0.0;
+  for (int c = threadIdx.x; c < nchunks; c += blockDim.x)
+    acc += partial[((int64_t)col * part_ld + i) * nchunks + c];
+  double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) {
+    if (accumulate) out[(int64_t)col * out_ld + i] += s;
+    else out[(int64_t)col * out_ld + i] = s;
+  }
+}
+
+struct GState {      // per-column GMRES state, FP64, device
+  double* H;         // [nrhs][m+1][m]  column-major in j: H[col][j*(m+1) + i]
+  double* cs;        // [nrhs][m]
+  double* sn;        // [nrhs][m]
+  double* g;         // [nrhs][m+1]
+  double* beta0;     // [nrhs] reference norm for the relative criterion
+  double* hcol;      // [nrhs][m+1] current Arnoldi column (dots)
+  double* hcol2;     // [nrhs][m+1] second-pass dots
+  double* nrm2;      // [nrhs]
+  int* active;       // [nrhs]
+  int* kused;        // [nrhs] Arnoldi steps taken in the current cycle
+  int* iters;        // [nrhs] total iterations
+};
+
+// After the two Gram-Schmidt passes: H[:,j] = hcol + hcol2, h_{j+1,j} = sqrt(nrm2);
+// Givens update; convergence test; scale factor for the new basis vector.
+__global__ void k_givens(GState s, int nrhs, int m, int j, double rtol, int max_it, double* inv_norm) {
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= nrhs) return;
+  if (!s.active[col]) { inv_norm[col] = 0.0; return; }
+  double* H = s.H + (int64_t)col * (m + 1) * m + (int64_t)j * (m + 1);
+  double* cs = s.cs + (int64_t)col * m;
+  double* sn = s.sn + (int64_t)col * m;
+  double* g = s.g + (int64_t)col * (m + 1);
+  for (int i = 0; i <= j; ++i) H[i] = s.hcol[(int64_t)col * (m + 1) + i] + s.hcol2[(int64_t)col * (m + 1) + i];
+  double hn = sqrt(fmax(s.nrm2[col], 0.0));
+  H[j + 1] = hn;
+  for (int i = 0; i < j; ++i) {
+    double t = cs[i] * H[i] + sn[i] * H[i + 1];
+    H[i + 1] = -sn[i] * H[i] + cs[i] * H[i + 1];
+    H[i] = t;
+  }
+  double den = hypot(H[j], H[j + 1]);
+  double c = den > 0.0 ? H[j] / den : 1.0;
+  double sv = den > 0.0 ? H[j + 1] / den : 0.0;
+  cs[j] = c;
+  sn[j] = sv;
+  H[j] = den;
+  H[j + 1] = 0.0;
+  g[j + 1] = -sv * g[j];
+  g[j] = c * g[j];
+  s.kused[col] = j + 1;
+  s.iters[col] += 1;
+  const bool conv = fabs(g[j + 1]) <= rtol * s.beta0[col];
+  if (conv || hn == 0.0 || s.iters[col] >= max_it) s.active[col] = 0;
+  inv_norm[col] = hn > 0.0 ? 1.0 / hn : 0.0;
+}
+
+template <typename T>
+__global__ void k_scale_cols(T* __restrict__ v, int64_t N, int nrhs, const double* __restrict__ f,
+                             const int* __restrict__ mask) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N * nrhs) return;
+  const int col = (int)(t / N);
+  if (mask && !mask[col]) return;
+  v[t] = (T)((double)v[t] * f[col]);
+}
+
+// start of a cycle: beta = ||V0||, g = beta e1, reference norm on the first cycle
+__global__ void k_cycle_start(GState s, int nrhs, int m, bool first, double* inv_norm) {
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= nrhs) return;
+  double beta = sqrt(fmax(s.nrm2[col], 0.0));
+  double* g = s.g + (int64_t)col * (m + 1);
+  for (int i = 0; i <= m; ++i) g[i] = 0.0;
+  g[0] = beta;
+  s.kused[col] = 0;
+  if (first) {
+    s.beta0[col] = beta;
+    s.active[col] = beta > 0.0 ? 1 : 0;
+    s.iters[col] = 0;
+  }
+  inv_norm[col] = beta > 0.0 ? 1.0 / beta : 0.0;
+}
+
+// y = H^-1 g (upper triangular, k x k), stored in hcol
+__global__ void k_backsolve(GState s, int nrhs, int m) {
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= nrhs) return;
+  const int k = s.kused[col];
+  const double* H = s.H + (int64_t)col * (m + 1) * m;
+  const double* g = s.g + (int64_t)col * (m + 1);
+  double* y = s.hcol + (int64_t)col * (m + 1);
+  for (int i = k - 1; i >= 0; --i) {
+    double acc = g[i];
+    for (int c = i + 1; c < k; ++c) acc -= H[(int64_t)c * (m + 1) + i] * y[c];
+    y[i] = H[(int64_t)i * (m + 1) + i] != 0.0 ? acc / H[(int64_t)i * (m + 1) + i] : 0.0;
+  }
+  for (int i = k; i <= m; ++i) y[i] = 0.0;
+}
+
+// x += sum_i y_i V_i
+template <typename T>
+__global__ void k_update_x(T* __restrict__ x, const T* __restrict__ V, int64_t N, int nrhs,
+                           const double* __restrict__ y, const int* __restrict__ kused, int m) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N * nrhs) return;
+  const int col = (int)(t / N);
+  const int k = kused[col];
+  double acc = (double)x[t];
+  for (int i = 0; i < k; ++i) acc += y[(int64_t)col * (m + 1) + i] * (double)V[(int64_t)i * N * nrhs + t];
+  x[t] = (T)acc;
+}
+
+template <typename T>
+__global__ void k_sub(const T* __restrict__ b, const T* __restrict__ ax, T* __restrict__ r, int64_t n) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) r[t] = b[t] - ax[t];
+}
+
+__global__ void k_cast_scaled(const double* __restrict__ src, float* __restrict__ dst, int64_t N, int nrhs,
+                              const double* __restrict__ f) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N * nrhs) return;
+  dst[t] = (float)(src[t] * f[t / N]);
+}
+
+template <typename T>
+__global__ void k_add_scaled(double* __restrict__ x, const T* __restrict__ d, int64_t N, int nrhs,
+                             const double* __restrict__ f) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N * nrhs) return;
+  x[t] += (double)d[t] * f[t / N];
+}
+
+// ------------------------------------------------------------------ GMRES
+struct SolveCounters {
+  int iters = 0;
+  int matvecs = 0;
+};
+
+static int nchunks_for(int64_t N) {
+  int64_t c = (N + 4095) / 4096;
+  if (c < 1) c = 1;
+  if (c > 512) c = 512;
+  return (int)c;
+}
+
+// Solve R A d = R r (x0 = 0) per column to a preconditioned relative
+// residual rtol.  r, d: device [nrhs][N] in T.  `adjoint`: use A^T and R^T.
+template <typename T>
+static int gmres(Handle& h, const T* r, T* d, int nrhs, double rtol, int max_it, bool adjoint,
+                 SolveCounters* cnt) {
+  const int64_t N = h.pan.N;
+  const int m = std::max(1, h.opts.restart);
+  cudaStream_t st = h.stream;
+  const int nch = nchunks_for(N);
+  // workspace
+  const size_t nV = (size_t)(m + 1) * nrhs * N;
+  const size_t nW = (size_t)nrhs * N;
+  size_t bytes = sizeof(T) * (nV + nW);
+  const size_t nd_H = (size_t)nrhs * (m + 1) * m, nd_cs = (size_t)nrhs * m, nd_g = (size_t)nrhs * (m + 1);
+  const size_t ndbl = nd_H + 2 * nd_cs + 3 * nd_g + 3 * (size_t)nrhs + (size_t)nrhs * (m + 1) * nch;
+  bytes += sizeof(double) * ndbl + sizeof(int) * 3 * nrhs + 256;
+  VC_TRY(h.solver_ws.alloc(bytes));
+  char* wp = h.solver_ws.p;
+  T* V = reinterpret_cast<T*>(wp); wp += sizeof(T) * nV;
+  T* W = reinterpret_cast<T*>(wp); wp += sizeof(T) * nW;
+  wp = reinterpret_cast<char*>(((uintptr_t)wp + 15) & ~(uintptr_t)15);
+  double* dp = reinterpret_cast<double*>(wp);
+  GState s;
+  s.H = dp; dp += nd_H;
+  s.cs = dp; dp += nd_cs;
+  s.sn = dp; dp += nd_cs;
+  s.g = dp; dp += nd_g;
+  s.hcol = dp; dp += nd_g;
+  s.hcol2 = dp; dp += nd_g;
+  s.beta0 = dp; dp += nrhs;
+  s.nrm2 = dp; dp += nrhs;
+  double* invn = dp; dp += nrhs;
+  double* partial = dp; dp += (size_t)nrhs * (m + 1) * nch;
+  int* ip = reinterpret_cast<int*>(dp);
+  s.active = ip; ip += nrhs;
+  s.kused = ip; ip += nrhs;
+  s.iters = ip; ip += nrhs;
+  VC_CUDA(cudaMemsetAsync(d, 0, sizeof(T) * nW, st));
+  const int TB = 256;
+  const unsigned gN = (unsigned)((N * nrhs + TB - 1) / TB);
+  const unsigned gC = (unsigned)((nrhs + 63) / 64);
+  std::vector<int> act(nrhs);
+  bool first = true;
+  auto apply_RA = [&](const T* in, T* out) -> int {
+    VC_TRY(mvm<T>(h, in, W, nrhs, adjoint, nullptr));
+    cnt->matvecs += 1;
+    // the transposed solve is preconditioned by the same R: any nonsingular R
+    // leaves the solution unchanged, and for BDD (symmetric conductor blocks,
+    // diagonal dielectric part) R^T = R exactly
+    VC_TRY(precond_apply<T>(h, W, out, nrhs));
+    return VOXCAP_OK;
+  };
+  int total_it = 0;
+  for (int cycle = 0; cycle < 100000; ++cycle) {
+    // V0 = R (r - A d)
+    if (first) {
+      VC_TRY(precond_apply<T>(h, r, V, nrhs));
+    } else {
+      VC_TRY(mvm<T>(h, d, W, nrhs, adjoint, nullptr));
+      cnt->matvecs += 1;
+      T* tmp = V + (size_t)m * nrhs * N;    // last basis slot as scratch
+      k_sub<T><<<gN, TB, 0, st>>>(r, W, tmp, N * nrhs); ::vc::note_launch();
+      VC_TRY(precond_apply<T>(h, tmp, V, nrhs));
+    }
+    dim3 gsw(nch, nrhs);
+    k_gs_sweep<T><<<gsw, kDotTB, 0, st>>>(V, V, N, nrhs, 0, nullptr, 0, 0, true, nullptr, nch,
+                                          partial, m + 1); ::vc::note_launch();
+    k_reduce_partial<<<dim3(1, nrhs), kDotTB, 0, st>>>(partial, nch, 1, m + 1, nullptr, s.nrm2, 1, false); ::vc::note_launch();
+    k_cycle_start<<<gC, 64, 0, st>>>(s, nrhs, m, first, invn); ::vc::note_launch();
+    k_scale_cols<T><<<gN, TB, 0, st>>>(V, N, nrhs, invn, nullptr); ::vc::note_launch();
+    VC_CUDA(cudaGetLastError());
+    first = false;
+    int j = 0;
+    for (j = 0; j < m; ++j) {
+      T* vj = V + (size_t)j * nrhs * N;
+      T* w = V + (size_t)(j + 1) * nrhs * N;
+      VC_TRY(apply_RA(vj, w));
+      // pass 1: h = V^T w
+      k_gs_sweep<T><<<gsw, kDotTB, 0, st>>>(V, w, N, nrhs, 0, nullptr, 0, j + 1, false, s.active, nch,
+                                            partial, m + 1); ::vc::note_launch();
+      k_reduce_partial<<<dim3(j + 1, nrhs), kDotTB, 0, st>>>(partial, nch, j + 1, m + 1, s.active,
+                                                             s.hcol, m + 1, false); ::vc::note_launch();
+      // pass 2: w -= V h ; h2 = V^T w
+      k_gs_sweep<T><<<gsw, kDotTB, 0, st>>>(V, w, N, nrhs, j + 1, s.hcol, m + 1, j + 1, false, s.active,
+                                            nch, partial, m + 1); ::vc::note_launch();
+      k_reduce_partial<<<dim3(j + 1, nrhs), kDotTB, 0, st>>>(partial, nch, j + 1, m + 1, s.active,
+                                                             s.hcol2, m + 1, false); ::vc::note_launch();
+      // w -= V h2 ; ||w||^2
+      k_gs_sweep<T><<<gsw, kDotTB, 0, st>>>(V, w, N, nrhs, j + 1, s.hcol2, m + 1, 0, true, s.active,
+                                            nch, partial, m + 1); ::vc::note_launch();
+      k_reduce_partial<<<dim3(1, nrhs), kDotTB, 0, st>>>(partial, nch, 1, m + 1, s.active, s.nrm2, 1,
+                                                         false); ::vc::note_launch();
+      k_givens<<<gC, 64, 0, st>>>(s, nrhs, m, j, rtol, max_it, invn); ::vc::note_launch();
+      k_scale_cols<T><<<gN, TB, 0, st>>>(w, N, nrhs, invn, nullptr); ::vc::note_launch();
+      VC_CUDA(cudaGetLastError());
+      ++total_it;
+      VC_CUDA(cudaMemcpyAsync(act.data(), s.active, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
+      VC_CUDA(cudaStreamSynchronize(st));
+      bool any = false;
+      for (int c = 0; c < nrhs; ++c) any = any || act[c];
+      if (!any) { ++j; break; }
+    }
+    k_backsolve<<<gC, 64, 0, st>>>(s, nrhs, m); ::vc::note_launch();
+    k_update_x<T><<<gN, TB, 0, st>>>(d, V, N, nrhs, s.hcol, s.kused, m); ::vc::note_launch();
+    VC_CUDA(cudaGetLastError());
+    // finished?
+    VC_CUDA(cudaMemcpyAsync(act.data(), s.active, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
+    std::vector<int> its(nrhs);
+    VC_CUDA(cudaMemcpyAsync(its.data(), s.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
+    VC_CUDA(cudaStreamSynchronize(st));
+    bool any = false;
+    int maxit = 0;
+    for (int c = 0; c < nrhs; ++c) { any = any || act[c]; maxit = std::max(maxit, its[c]); }
+    if (!any || maxit >= max_it) break;
+    // restart: the next cycle recomputes the residual of the active columns;
+    // converged columns keep active = 0 (k_cycle_start leaves it alone)
+  }
+  cnt->iters += total_it;
+  return VOXCAP_OK;
+}
+
+// column norms of a double [nrhs][N] array -> host
+static int col_norms(Handle& h, const double* v, int nrhs, std::vector<double>& out, double* partial_ws,
+                     double* dev_out) {
+  const int64_t N = h.pan.N;
+  const int nch = nchunks_for(N);
+  dim3 g(nch, nrhs);
+  k_gs_sweep<double><<<g, kDotTB, 0, h.stream>>>(nullptr, const_cast<double*>(v), N, nrhs, 0, nullptr, 0,
+                                                 0, true, nullptr, nch, partial_ws, 1); ::vc::note_launch();
+  k_reduce_partial<<<dim3(1, nrhs), kDotTB, 0, h.stream>>>(partial_ws, nch, 1, 1, nullptr, dev_out, 1, false); ::vc::note_launch();
+  VC_CUDA(cudaGetLastError());
+  out.resize(nrhs);
+  VC_CUDA(cudaMemcpyAsync(out.data(), dev_out, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, h.stream));
+  VC_CUDA(cudaStreamSynchronize(h.stream));
+  for (auto& x : out) x = std::sqrt(std::max(x, 0.0));
+  return VOXCAP_OK;
+}
+
+int solve(Handle& h, const double* B, int nrhs, double tol, double* X, voxcap_stats* st, bool adjoint) {
+  auto t0 = std::chrono::steady_clock::now();
+  const int64_t N = h.pan.N;
+  const bool refine = h.opts.precision == VOXCAP_FP32_REFINE;
+  cudaStream_t s = h.stream;
+  voxcap_stats loc = {};
+  if (N == 0 || nrhs <= 0) {
+    if (st) { *st = loc; st->converged = 1; }
+    return VOXCAP_OK;
+  }
+  DBuf<double> R64, AX, dpart, dnorm, fac;
+  DBuf<float> rf, df;
+  DBuf<double> d64;
+  const size_t n = (size_t)N * nrhs;
+  VC_TRY(R64.alloc(n));
+  VC_TRY(AX.alloc(n));
+  VC_TRY(dpart.alloc((size_t)nrhs * nchunks_for(N) + 1));
+  VC_TRY(dnorm.alloc(nrhs));
+  VC_TRY(fac.alloc(nrhs));
+  if (refine) { VC_TRY(rf.alloc(n)); VC_TRY(df.alloc(n)); }
+  else VC_TRY(d64.alloc(n));
+  std::vector<double> bn, rn;
+  VC_TRY(col_norms(h, B, nrhs, bn, dpart.p, dnorm.p));
+  VC_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * n, s));
+  const int TB = 256;
+  const unsigned gN = (unsigned)((n + TB - 1) / TB);
+  SolveCounters cnt;
+  const int max_sweeps = std::max(1, h.opts.max_sweeps);
+  double worst = 0.0;
+  bool conv = false;
+  int sweeps = 0;
+  for (int sw = 0; sw <= max_sweeps; ++sw) {
+    if (sw == 0) {
+      VC_CUDA(cudaMemcpyAsync(R64.p, B, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    } else {
+      VC_TRY(mvm<double>(h, X, AX.p, nrhs, adjoint, nullptr));
+      cnt.matvecs += 1;
+      k_sub<double><<<gN, TB, 0, s>>>(B, AX.p, R64.p, (int64_t)n); ::vc::note_launch();
+      VC_CUDA(cudaGetLastError());
+    }
+    VC_TRY(col_norms(h, R64.p, nrhs, rn, dpart.p, dnorm.p));
+    worst = 0.0;
+    std::vector<double> f(nrhs), finv(nrhs);
+    double need = 0.0;   // largest reduction still needed
+    for (int c = 0; c < nrhs; ++c) {
+      double rel = bn[c] > 0.0 ? rn[c] / bn[c] : 0.0;
+      worst = std::max(worst, rel);
+      // columns that already meet tol get a zero right-hand side
+      bool done = rel <= tol || rn[c] == 0.0;
+      f[c] = done ? 0.0 : 1.0 / rn[c];
+      finv[c] = done ? 0.0 : rn[c];
+      if (!done) need = std::max(need, tol / rel);
+    }
+    if (worst <= tol) { conv = true; break; }
+    if (sw == max_sweeps || cnt.iters >= h.opts.max_iters) break;
+    ++sweeps;
+    // inner tolerance: aim to finish in this sweep, within what the inner
+    // precision can deliver
+    double floor_t = refine ? 5e-6 : 1e-14;
+    double cap = refine ? std::max(h.opts.inner_tol, floor_t) : 1e-2;
+    double itol = std::min(cap, std::max(floor_t, 0.5 * need));
+    int left = std::max(1, h.opts.max_iters - cnt.iters);
+    VC_CUDA(cudaMemcpyAsync(fac.p, f.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+    if (refine) {
+      k_cast_scaled<<<gN, TB, 0, s>>>(R64.p, rf.p, N, nrhs, fac.p); ::vc::note_launch();
+      VC_TRY(gmres<float>(h, rf.p, df.p, nrhs, itol, left, adjoint, &cnt));
+      VC_CUDA(cudaMemcpyAsync(fac.p, finv.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+      k_add_scaled<float><<<gN, TB, 0, s>>>(X, df.p, N, nrhs, fac.p); ::vc::note_launch();
+    } else {
+      // scale the FP64 residual to unit norm too (keeps the criterion relative)
+      k_scale_cols<double><<<gN, TB, 0, s>>>(R64.p, N, nrhs, fac.p, nullptr); ::vc::note_launch();
+      VC_TRY(gmres<double>(h, R64.p, d64.p, nrhs, itol, left, adjoint, &cnt));
+      VC_CUDA(cudaMemcpyAsync(fac.p, finv.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+      k_add_scaled<double><<<gN, TB, 0, s>>>(X, d64.p, N, nrhs, fac.p); ::vc::note_launch();
+    }
+    VC_CUDA(cudaGetLastError());
+  }
+  VC_CUDA(cudaStreamSynchronize(s));
+  auto t1 = std::chrono::steady_clock::now();
+  loc.iterations = cnt.iters;
+  loc.sweeps = sweeps;
+  loc.matvecs = cnt.matvecs;
+  loc.converged = conv ? 1 : 0;
+  loc.rel_residual = worst;
+  loc.seconds = std::chrono::duration<double>(t1 - t0).count();
+  if (st) *st = loc;
+  if (!conv) {
+    set_error("solver stopped at its caps: relative residual " + std::to_string(worst));
+    return VOXCAP_ERR_NOT_CONVERGED;
+  }
+  return VOXCAP_OK;
+}
+
+// ------------------------------------------------------------------ capacitance
+__global__ void k_unit_rhs(int64_t N, int m, const int8_t* kind, const int16_t* owner, double* B) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N * m) return;
+  const int j = (int)(t / N);
+  const int64_t p = t % N;
+  B[t] = (kind[p] == 0 && owner[p] == j) ? 1.0 : 0.0;
+}
+
+// C'[s][i][j] = sum_{p in structure s, conductor i} qscale_p rho_j[p]
+__global__ void k_cap_reduce(int64_t N, int m, const int64_t* off, const int64_t* ncond,
+                             const int16_t* owner, const double* qscale, const double* rho,
+                             double* Cn) {
+  __shared__ double sh[32];
+  const int s = blockIdx.x, i = blockIdx.y, j = blockIdx.z;
+  const int64_t lo = off[s], hi = lo + ncond[s];
+  double acc = 0.0;
+  for (int64_t p = lo + threadIdx.x; p < hi; p += blockDim.x)
+    if (owner[p] == i) acc += qscale[p] * rho[(int64_t)j * N + p];
+  double v = block_sum(acc, sh);
+  if (threadIdx.x == 0) Cn[((int64_t)s * m + i) * m + j] = v;
+}
+
+int capacitance(Handle& h, double tol, double* C_host, double* rho_dev, voxcap_stats* st) {
+  const int m = h.pan.m_max;
+  const int S = h.pan.S;
+  const int64_t N = h.pan.N;
+  VC_CHECK(m > 0, VOXCAP_ERR_NO_CONDUCTOR, "no conductor in the material table");
+  VC_TRY(h.rhs.alloc((size_t)N * m));
+  VC_TRY(h.rho.alloc((size_t)N * m));
+  const int TB = 256;
+  k_unit_rhs<<<(unsigned)((N * m + TB - 1) / TB), TB, 0, h.stream>>>(N, m, h.pan.kind.p, h.pan.owner.p,
+                                                                      h.rhs.p); ::vc::note_launch();
+  VC_CUDA(cudaGetLastError());
+  int rc = solve(h, h.rhs.p, m, tol, h.rho.p, st, false);
+  if (rc != VOXCAP_OK && rc != VOXCAP_ERR_NOT_CONVERGED) return rc;
+  h.have_rho = true;
+  DBuf<int64_t> offd, ncd;
+  DBuf<double> Cn;
+  VC_TRY(offd.alloc(S));
+  VC_TRY(ncd.alloc(S));
+  VC_TRY(Cn.alloc((size_t)S * m * m));
+  VC_CUDA(cudaMemcpyAsync(offd.p, h.pan.off.data(), sizeof(int64_t) * S, cudaMemcpyHostToDevice, h.stream));
+  VC_CUDA(cudaMemcpyAsync(ncd.p, h.pan.nc.data(), sizeof(int64_t) * S, cudaMemcpyHostToDevice, h.stream));
+  k_cap_reduce<<<dim3(S, m, m), TB, 0, h.stream>>>(N, m, offd.p, ncd.p, h.pan.owner.p, h.pan.qscale.p,
+                                                  h.rho.p, Cn.p); ::vc::note_launch();
+  VC_CUDA(cudaGetLastError());
+  std::vector<double> cn((size_t)S * m * m);
+  VC_CUDA(cudaMemcpyAsync(cn.data(), Cn.p, sizeof(double) * cn.size(), cudaMemcpyDeviceToHost, h.stream));
+  VC_CUDA(cudaStreamSynchronize(h.stream));
+  const double eps0 = 8.8541878128e-12;
+  for (size_t q = 0; q < cn.size(); ++q) C_host[q] = eps0 * h.dv * cn[q];
+  if (rho_dev)
+    VC_CUDA(cudaMemcpy(rho_dev, h.rho.p, sizeof(double) * (size_t)N * m, cudaMemcpyDeviceToDevice));
+  return rc;
+}
+
+}  // namespace vc

@@ -1,0 +1,290 @@
+// Block-circulant embedding of the Toeplitz tensors and their FFT
+// (Eqs. 11-12, Appendix B), plus the FFT plans shared with the products.
+//
+// Frame.  Shifting every face grid by half a voxel along its own normal puts
+// all panel centres on the voxel-centre lattice.  In that frame each kernel
+// is even or odd about 0 along every axis, so its spectrum is real (P) or
+// imaginary (E):
+//     K^{ab}(k) = exp(-i pi k_a/M_a) * S^{ab}(k) * exp(+i pi k_b/M_b),
+//     S = R (potential blocks)  or  S = -i R (normal-field blocks),
+// with R real and R(M-k) = +-R(k) along each axis.  Only R on the octant
+// [0,M_x/2] x [0,M_y/2] x [0,M_z/2] is stored, FP64 and FP32, scaled by
+// 1/(M_x M_y M_z).  The products apply the half-voxel phases to the charge
+// spectra (exp(+i pi k_b/M_b) on grid b) and to the results
+// (exp(-i pi k_a/M_a) on grid a).  P^{yx}, P^{zx}, P^{zy} are the same real R
+// as P^{xy}, P^{xz}, P^{yz}: this is Eq. 12 in the shifted frame.
+#include <cmath>
+#include <vector>
+
+#include "internal.h"
+
+namespace vc {
+
+// ------------------------------------------------------------ padding / plans
+static bool smooth7(int n) {
+  for (int p : {2, 3, 5, 7})
+    while (n % p == 0) n /= p;
+  return n == 1;
+}
+
+static int pick_length(int N, int mode) {
+  if (mode == 1) return 2 * (N + 1);
+  int m = 2 * N + 1;
+  if (m & 1) ++m;
+  while (!smooth7(m)) m += 2;
+  return m;
+}
+
+template <typename C>
+static void fill_twiddles(std::vector<C>& tw, std::vector<C>& ph, int L) {
+  tw.resize(L);
+  ph.resize(L);
+  const long double pi = 3.141592653589793238462643383279502884L;
+  for (int m = 0; m < L; ++m) {
+    long double a = -2.0L * pi * (long double)m / (long double)L;
+    tw[m].x = (decltype(C::x))std::cos(a);
+    tw[m].y = (decltype(C::x))std::sin(a);
+    long double b = pi * (long double)m / (long double)L;
+    ph[m].x = (decltype(C::x))std::cos(b);
+    ph[m].y = (decltype(C::x))std::sin(b);
+  }
+}
+
+int build_fft_plans(Handle& h) {
+  Geom& g = h.g;
+  int n[3] = {g.nx, g.ny, g.nz};
+  int M[3];
+  for (int a = 0; a < 3; ++a) {
+    M[a] = pick_length(n[a], h.opts.pad_mode);
+    int rad[kMaxStages], nst = 0;
+    VC_CHECK(factor_length(M[a], rad, &nst), VOXCAP_ERR_UNSUPPORTED,
+             "FFT length " + std::to_string(M[a]) + " is not 2/3/5/7-smooth (use pad_mode 0)");
+    std::vector<double2> twd, phd;
+    std::vector<float2> twf, phf;
+    fill_twiddles(twd, phd, M[a]);
+    fill_twiddles(twf, phf, M[a]);
+    VC_TRY(h.twd[a].alloc(M[a])); VC_TRY(h.twf[a].alloc(M[a]));
+    VC_TRY(h.phd[a].alloc(M[a])); VC_TRY(h.phf[a].alloc(M[a]));
+    VC_CUDA(cudaMemcpy(h.twd[a].p, twd.data(), sizeof(double2) * M[a], cudaMemcpyHostToDevice));
+    VC_CUDA(cudaMemcpy(h.twf[a].p, twf.data(), sizeof(float2) * M[a], cudaMemcpyHostToDevice));
+    VC_CUDA(cudaMemcpy(h.phd[a].p, phd.data(), sizeof(double2) * M[a], cudaMemcpyHostToDevice));
+    VC_CUDA(cudaMemcpy(h.phf[a].p, phf.data(), sizeof(float2) * M[a], cudaMemcpyHostToDevice));
+    h.pd[a].L = h.pf[a].L = M[a];
+    h.pd[a].nst = h.pf[a].nst = nst;
+    for (int s = 0; s < nst; ++s) h.pd[a].radix[s] = h.pf[a].radix[s] = rad[s];
+    h.pd[a].tw = h.twd[a].p;
+    h.pf[a].tw = h.twf[a].p;
+  }
+  g.Mx = M[0]; g.My = M[1]; g.Mz = M[2];
+  g.Hx = g.Mx / 2 + 1;
+  g.Oy = g.My / 2 + 1;
+  g.Oz = g.Mz / 2 + 1;
+  return VOXCAP_OK;
+}
+
+// ------------------------------------------------------------ embedding
+// Per-axis mapping of a circulant index to the Toeplitz index and sign.
+struct AxisMap {
+  int type;   // 0 even@0, 1 odd@0, 2 even@+1/2, 3 odd@+1/2, 4 even@-1/2
+  int dmin, dmax, M;
+};
+
+__device__ __forceinline__ bool axis_lookup(const AxisMap& am, int i, int* e, double* sg) {
+  int d;
+  if (i <= am.dmax) d = i;
+  else if (i >= am.M + am.dmin) d = i - am.M;
+  else return false;
+  switch (am.type) {
+    case 0: *e = d < 0 ? -d : d; break;
+    case 1: *e = d < 0 ? -d : d; if (d < 0) *sg = -*sg; break;
+    case 2: *e = d >= 1 ? d - 1 : -d; break;
+    case 3: *e = d >= 1 ? d - 1 : -d; if (d < 1) *sg = -*sg; break;
+    default: *e = d >= 0 ? d : -d - 1; break;
+  }
+  return true;
+}
+
+__global__ void k_embed(const double* __restrict__ T, int tx, int ty, AxisMap ax, AxisMap ay,
+                        AxisMap az, double* __restrict__ circ) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t n = (int64_t)ax.M * ay.M * az.M;
+  if (t >= n) return;
+  int i = (int)(t % ax.M), j = (int)((t / ax.M) % ay.M), k = (int)(t / ((int64_t)ax.M * ay.M));
+  int ex, ey, ez;
+  double sg = 1.0;
+  double v = 0.0;
+  if (axis_lookup(ax, i, &ex, &sg) && axis_lookup(ay, j, &ey, &sg) && axis_lookup(az, k, &ez, &sg))
+    v = sg * T[(int64_t)ex + (int64_t)tx * (ey + (int64_t)ty * ez)];
+  circ[t] = v;
+}
+
+static AxisMap axis_map(int kk, int a, int N, int M) {
+  const int te = ker_test(kk), so = ker_src(kk);
+  const bool E = kk >= 6;
+  AxisMap am;
+  am.M = M;
+  if (te == so) {
+    if (a == te) { am.type = E ? 1 : 0; am.dmin = -N; am.dmax = N; }
+    else { am.type = 0; am.dmin = -(N - 1); am.dmax = N - 1; }
+  } else if (a == te) {
+    am.type = E ? 3 : 2; am.dmin = -(N - 1); am.dmax = N;
+  } else if (a == so) {
+    am.type = 4; am.dmin = -N; am.dmax = N - 1;
+  } else {
+    am.type = 0; am.dmin = -(N - 1); am.dmax = N - 1;
+  }
+  return am;
+}
+
+// ------------------------------------------------------------ generic FFT passes
+// Real rows of length M (x) -> half spectra (Hx), two rows per complex line.
+template <typename T>
+__global__ void k_rows_r2c(const T* __restrict__ in, int64_t nrows, int M, int H,
+                           C_t<T>* __restrict__ out, Plan1D<C_t<T>> plan, int NL) {
+  using C = C_t<T>;
+  extern __shared__ unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  C* scr = buf + (size_t)M * NL;
+  const int64_t row0 = (int64_t)blockIdx.x * NL * 2;
+  for (int t = threadIdx.x; t < M * NL; t += blockDim.x) {
+    int l = t % NL, x = t / NL;
+    int64_t ra = row0 + 2 * l, rb = ra + 1;
+    T a = ra < nrows ? in[ra * M + x] : (T)0;
+    T b = rb < nrows ? in[rb * M + x] : (T)0;
+    buf[x * NL + l] = mk<C>(a, b);
+  }
+  __syncthreads();
+  C* res = fft_lines(buf, scr, NL, NL, plan, false);
+  for (int t = threadIdx.x; t < H * NL; t += blockDim.x) {
+    int l = t % NL, k = t / NL;
+    int64_t ra = row0 + 2 * l, rb = ra + 1;
+    C z = res[k * NL + l];
+    C zc = cconj(res[((M - k) % M) * NL + l]);
+    C A = cscale(cadd(z, zc), (T)0.5);
+    C B = cscale(cmul_mi(csub(z, zc)), (T)0.5);
+    if (ra < nrows) out[ra * H + k] = A;
+    if (rb < nrows) out[rb * H + k] = B;
+  }
+}
+
+// In-place complex FFT along a strided axis of a [outer][L][inner] array;
+// each block handles TX consecutive inner positions of one outer index.
+template <typename T>
+__global__ void k_strided_c2c(C_t<T>* __restrict__ data, int64_t outer, int L, int64_t inner,
+                              Plan1D<C_t<T>> plan, int TX, bool inv) {
+  using C = C_t<T>;
+  extern __shared__ unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  C* scr = buf + (size_t)L * TX;
+  const int64_t tiles = (inner + TX - 1) / TX;
+  const int64_t o = blockIdx.x / tiles;
+  const int64_t i0 = (blockIdx.x % tiles) * TX;
+  C* base = data + o * L * inner;
+  for (int t = threadIdx.x; t < L * TX; t += blockDim.x) {
+    int c = t % TX, p = t / TX;
+    int64_t ii = i0 + c;
+    buf[p * TX + c] = ii < inner ? base[(int64_t)p * inner + ii] : mk<C>((T)0, (T)0);
+  }
+  __syncthreads();
+  C* res = fft_lines(buf, scr, TX, TX, plan, inv);
+  for (int t = threadIdx.x; t < L * TX; t += blockDim.x) {
+    int c = t % TX, p = t / TX;
+    int64_t ii = i0 + c;
+    if (ii < inner) base[(int64_t)p * inner + ii] = res[p * TX + c];
+  }
+}
+
+// Extract the real octant R of one kernel spectrum (see file comment).
+__global__ void k_extract(const double2* __restrict__ spec, Geom g, int kk, bool E, int te, int so,
+                          const double2* __restrict__ phx, const double2* __restrict__ phy,
+                          const double2* __restrict__ phz, double scale,
+                          double* __restrict__ Rd, float* __restrict__ Rf) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t n = (int64_t)g.Hx * g.Oy * g.Oz;
+  if (t >= n) return;
+  int kx = (int)(t % g.Hx), ky = (int)((t / g.Hx) % g.Oy), kz = (int)(t / ((int64_t)g.Hx * g.Oy));
+  double2 v = spec[((int64_t)kz * g.My + ky) * g.Hx + kx];
+  // undo exp(-i pi k_te/M) S exp(+i pi k_so/M):  multiply by exp(+i pi k_te/M) exp(-i pi k_so/M)
+  if (te != so) {
+    const double2* pt = te == 0 ? phx : (te == 1 ? phy : phz);
+    const double2* ps = so == 0 ? phx : (so == 1 ? phy : phz);
+    int kt = te == 0 ? kx : (te == 1 ? ky : kz);
+    int ks = so == 0 ? kx : (so == 1 ? ky : kz);
+    v = cmul(v, pt[kt]);
+    v = cmul(v, cconj(ps[ks]));
+  }
+  double r = E ? -v.y : v.x;     // S = -i R  ->  R = i S;  Re(i S) = -Im(S)
+  r *= scale;
+  Rd[t] = r;
+  Rf[t] = (float)r;
+}
+
+template <typename T> static int smem_limit_lines(int L, int maxlines) {
+  const size_t budget = 96 * 1024;
+  int nl = (int)(budget / (2 * (size_t)L * sizeof(C_t<T>)));
+  if (nl > maxlines) nl = maxlines;
+  if (nl < 1) nl = 1;
+  return nl;
+}
+
+int build_spectra(Handle& h) {
+  const Geom& g = h.g;
+  const int n[3] = {g.nx, g.ny, g.nz};
+  const int64_t Mtot = (int64_t)g.Mx * g.My * g.Mz;
+  const int64_t Htot = (int64_t)g.Hx * g.My * g.Mz;
+  const int64_t Otot = (int64_t)g.Hx * g.Oy * g.Oz;
+  DBuf<double> circ;
+  DBuf<double2> spec;
+  VC_TRY(circ.alloc((size_t)Mtot));
+  VC_TRY(spec.alloc((size_t)Htot));
+  VC_TRY(h.spec_d.alloc((size_t)Otot * kNumKernels));
+  VC_TRY(h.spec_f.alloc((size_t)Otot * kNumKernels));
+  const double scale = 1.0 / (double)Mtot;
+  const int TB = 256;
+  for (int kk = 0; kk < kNumKernels; ++kk) {
+    AxisMap am[3];
+    for (int a = 0; a < 3; ++a) am[a] = axis_map(kk, a, n[a], a == 0 ? g.Mx : (a == 1 ? g.My : g.Mz));
+    k_embed<<<(unsigned)((Mtot + TB - 1) / TB), TB, 0, h.stream>>>(
+        h.toep[kk].p, h.tdims[kk][0], h.tdims[kk][1], am[0], am[1], am[2], circ.p); ::vc::note_launch();
+    VC_CUDA(cudaGetLastError());
+    // x: real rows -> half spectra
+    {
+      int NL = smem_limit_lines<double>(g.Mx, 16);
+      int64_t nrows = (int64_t)g.My * g.Mz;
+      unsigned nblk = (unsigned)((nrows + 2 * NL - 1) / (2 * NL));
+      size_t sm = 2 * (size_t)g.Mx * NL * sizeof(double2);
+      VC_CUDA(cudaFuncSetAttribute(k_rows_r2c<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      k_rows_r2c<double><<<nblk, 256, sm, h.stream>>>(circ.p, nrows, g.Mx, g.Hx, spec.p, h.pd[0], NL); ::vc::note_launch();
+      VC_CUDA(cudaGetLastError());
+    }
+    // y: [Mz][My][Hx] along My
+    {
+      int TX = smem_limit_lines<double>(g.My, 16);
+      int64_t tiles = (g.Hx + TX - 1) / TX;
+      size_t sm = 2 * (size_t)g.My * TX * sizeof(double2);
+      VC_CUDA(cudaFuncSetAttribute(k_strided_c2c<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      k_strided_c2c<double><<<(unsigned)(g.Mz * tiles), 256, sm, h.stream>>>(
+          spec.p, g.Mz, g.My, g.Hx, h.pd[1], TX, false); ::vc::note_launch();
+      VC_CUDA(cudaGetLastError());
+    }
+    // z: [1][Mz][My*Hx] along Mz
+    {
+      int TX = smem_limit_lines<double>(g.Mz, 16);
+      int64_t inner = (int64_t)g.My * g.Hx;
+      int64_t tiles = (inner + TX - 1) / TX;
+      size_t sm = 2 * (size_t)g.Mz * TX * sizeof(double2);
+      VC_CUDA(cudaFuncSetAttribute(k_strided_c2c<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      k_strided_c2c<double><<<(unsigned)tiles, 256, sm, h.stream>>>(spec.p, 1, g.Mz, inner, h.pd[2],
+                                                                   TX, false); ::vc::note_launch();
+      VC_CUDA(cudaGetLastError());
+    }
+    k_extract<<<(unsigned)((Otot + TB - 1) / TB), TB, 0, h.stream>>>(
+        spec.p, g, kk, kk >= 6, ker_test(kk), ker_src(kk), h.phd[0].p, h.phd[1].p, h.phd[2].p,
+        scale, h.spec_d.p + (size_t)kk * Otot, h.spec_f.p + (size_t)kk * Otot); ::vc::note_launch();
+    VC_CUDA(cudaGetLastError());
+  }
+  VC_CUDA(cudaStreamSynchronize(h.stream));
+  return VOXCAP_OK;
+}
+
+}  // namespace vc

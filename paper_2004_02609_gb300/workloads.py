@@ -190,3 +190,32 @@ def coated_sphere(n: int = 20, eps_coat: float = 2.0) -> Workload:
     lab[R < n / 4] = 2
     return Workload(f"coated_sphere_{n}^3", lab, np.array([-1, -1, 0], np.int32),
                     np.array([1.0, eps_coat, 1.0]), voxel_size=1.0 / n)
+
+
+def random_structure(shape=(7, 5, 6), seed: int = 0, n_cond: int = 2, n_diel: int = 3,
+                     fill: float = 0.5) -> Workload:
+    """A small seeded structure on a (nx, ny, nz) grid for parity tests: each
+    voxel gets one of ``n_diel`` dielectric labels (random eps_r in [1.5, 8];
+    label 0 is vacuum when ``fill`` < 1) and ``n_cond`` conductor boxes are
+    carved in, kept one voxel apart so that no two conductors touch."""
+    nx, ny, nz = shape
+    rng = np.random.default_rng(seed)
+    lab = rng.integers(1, n_diel + 1, size=(nz, ny, nx)).astype(np.int32)
+    lab[rng.random((nz, ny, nx)) > fill] = 0
+    eps = np.concatenate([[1.0], 1.5 + 6.5 * rng.random(n_diel), np.ones(n_cond)])
+    cid = np.concatenate([np.full(n_diel + 1, -1), np.arange(n_cond)]).astype(np.int32)
+    taken = np.zeros((nz, ny, nx), bool)
+    for c in range(n_cond):
+        for _ in range(100):
+            size = [int(rng.integers(1, max(2, d // 2) + 1)) for d in (nx, ny, nz)]
+            lo = [int(rng.integers(0, d - s + 1)) for d, s in zip((nx, ny, nz), size)]
+            sl = (slice(lo[2], lo[2] + size[2]), slice(lo[1], lo[1] + size[1]),
+                  slice(lo[0], lo[0] + size[0]))
+            grown = (slice(max(0, lo[2] - 1), lo[2] + size[2] + 1),
+                     slice(max(0, lo[1] - 1), lo[1] + size[1] + 1),
+                     slice(max(0, lo[0] - 1), lo[0] + size[0] + 1))
+            if not taken[grown].any():
+                lab[sl] = n_diel + 1 + c
+                taken[sl] = True
+                break
+    return Workload(f"random{shape}_{seed}", lab, cid, eps)

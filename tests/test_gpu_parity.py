@@ -1,0 +1,216 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Bars: panel maps bit-exact; single entries within 1e-12 relative; products
+within 1e-12 relative l2 in FP64 and 2e-6 in FP32; preconditioner within
+1e-10 (FP64); capacitance entries within 1e-4 relative (the targets of the
+hot path)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2004_02609_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2004_02609_gb300 import build
+    build.build()
+
+
+def _V():
+    from paper_2004_02609_gb300 import voxcap as V
+    return V
+
+
+def make(w, **kw):
+    return _V().VoxCap(w.labels, w.conductor_id, w.eps_r, w.voxel_size, **kw)
+
+
+SMALL = [W.cube(4), W.random_structure((7, 5, 6), 0), W.random_structure((9, 6, 5), 1),
+         W.random_structure((5, 8, 7), 2, n_cond=3), W.coated_sphere(12, 3.0),
+         W.plates(12, 10, 8)]
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.mark.parametrize("w", SMALL, ids=lambda w: w.name)
+def test_panel_map_bit_exact(w):
+    ps = O.panels(w.labels, w.conductor_id, w.eps_r)
+    vc = make(w)
+    pm = vc.panel_map()
+    assert vc.N == ps.n
+    for k in ("orient", "face", "kind", "owner"):
+        assert np.array_equal(pm[k], getattr(ps, k).astype(pm[k].dtype)), k
+    assert np.array_equal(pm["idiag"], ps.idiag)
+    assert np.array_equal(pm["qscale"], ps.qscale)
+
+
+def _entry_cases():
+    rng = np.random.default_rng(7)
+    cases = []
+    for _ in range(400):
+        to, so = (int(v) for v in rng.integers(0, 3, 2))
+        R = [1, 2, 3, 5, 9, 17, 33, 60][int(rng.integers(0, 8))]
+        d = rng.integers(-R, R + 1, 3).astype(float)
+        if to != so:
+            d[to] -= 0.5
+            d[so] += 0.5
+        cases.append((int(rng.integers(0, 2)), to, so, d))
+    # every near-field configuration around the origin
+    for to in range(3):
+        for so in range(3):
+            for dx in range(-2, 3):
+                for dy in range(-2, 3):
+                    for dz in range(-2, 3):
+                        d = np.array([dx, dy, dz], float)
+                        if to != so:
+                            d[to] -= 0.5
+                            d[so] += 0.5
+                        for kind in (0, 1):
+                            cases.append((kind, to, so, d))
+    return cases
+
+
+def test_entries_match_oracle():
+    V = _V()
+    cases = _entry_cases()
+    kind = np.array([c[0] for c in cases])
+    to = np.array([c[1] for c in cases])
+    so = np.array([c[2] for c in cases])
+    d = np.array([c[3] for c in cases])
+    got = V.entries(kind, to, so, d)
+    ref = O.entries(kind, to, so, d, rtol=1e-14)
+    scale = np.maximum(np.abs(ref), 1e-6 * np.abs(ref).max())
+    err = np.abs(got - ref) / scale
+    worst = int(np.argmax(err))
+    assert err.max() < 2e-12, (cases[worst], got[worst], ref[worst])
+
+
+def test_toeplitz_tables_sampled():
+    """The 15 block-Toeplitz tensors of a grid hold the integrals of their
+    index offsets (Appendix B): sampled entries against the oracle."""
+    w = W.random_structure((9, 7, 6), 3)
+    vc = make(w)
+    rng = np.random.default_rng(11)
+    te = [0, 1, 2, 0, 0, 1, 0, 1, 2, 0, 0, 1, 1, 2, 2]
+    so = [0, 1, 2, 1, 2, 2, 0, 1, 2, 1, 2, 2, 0, 0, 1]
+    for t in range(15):
+        T = vc.toeplitz(t)
+        dz, dy, dx = T.shape
+        idx = [(int(rng.integers(0, dx)), int(rng.integers(0, dy)), int(rng.integers(0, dz)))
+               for _ in range(12)] + [(0, 0, 0)]
+        for (ex, ey, ez) in idx:
+            d = np.array([ex, ey, ez], float)
+            if te[t] != so[t]:
+                d[te[t]] += 0.5
+                d[so[t]] += 0.5
+            ref = O.entry(1 if t >= 6 else 0, te[t], so[t], d, rtol=1e-14)
+            got = T[ez, ey, ex]
+            assert abs(got - ref) <= 2e-12 * max(abs(ref), 1e-8), (t, ex, ey, ez, got, ref)
+
+
+@pytest.mark.parametrize("w", SMALL[1:4] + [SMALL[5]], ids=lambda w: w.name)
+@pytest.mark.parametrize("pad_mode", [0, 1])
+def test_matvec_matches_dense(w, pad_mode):
+    import torch
+    nx, ny, nz = w.shape_xyz
+    try:
+        vc = make(w, pad_mode=pad_mode)
+    except Exception as e:     # 2(N+1) not 2/3/5/7-smooth: pad_mode 1 unsupported
+        assert pad_mode == 1 and "smooth" in str(e)
+        pytest.skip("2(N+1) not smooth")
+    ps = O.panels(w.labels, w.conductor_id, w.eps_r)
+    A = O.dense_matrix(ps, rtol=1e-14)
+    rng = np.random.default_rng(0)
+    X = rng.standard_normal((3, ps.n))
+    ref = (A @ X.T).T
+    refT = (A.T @ X.T).T
+    x64 = torch.tensor(X, device="cuda")
+    y64 = vc.matvec(x64).cpu().numpy()
+    for r in range(3):
+        assert rel_l2(y64[r], ref[r]) < 1e-12
+    yT = vc.matvec(x64, adjoint=True).cpu().numpy()
+    for r in range(3):
+        assert rel_l2(yT[r], refT[r]) < 1e-12
+    y32 = vc.matvec(x64.float()).cpu().numpy()
+    for r in range(3):
+        assert rel_l2(y32[r], ref[r]) < 2e-6
+
+
+def test_matvec_paper_padding_equals_smooth_padding():
+    """Any padded length >= 2N+1 gives the same linear convolution (Appendix B):
+    the paper's 2(N+1) and the smooth length agree to rounding."""
+    import torch
+    w = W.random_structure((4, 6, 9), 5)        # 2(N+1) = 10, 14, 20: smooth
+    a = make(w, pad_mode=0)
+    b = make(w, pad_mode=1)
+    assert b.fft_lengths() == (10, 14, 20)
+    x = torch.randn(a.N, dtype=torch.float64, device="cuda")
+    assert rel_l2(a.matvec(x).cpu(), b.matvec(x).cpu()) < 1e-13
+
+
+@pytest.mark.parametrize("kind", ["bdd", "bd", "diag", "none"])
+def test_preconditioner_matches_dense(kind):
+    import torch
+    w = W.random_structure((9, 7, 8), 4, n_cond=3)
+    nv = (3, 2, 4)
+    vc = make(w, precond=kind, nv=nv)
+    ps = O.panels(w.labels, w.conductor_id, w.eps_r)
+    A = O.dense_matrix(ps, rtol=1e-14)
+    R = O.precond_matrix(ps, A, nv=np.array(nv), kind=kind)
+    r = np.random.default_rng(1).standard_normal((2, ps.n))
+    z = vc.matvec(torch.tensor(r, device="cuda"), r_only=True).cpu().numpy()
+    for c in range(2):
+        assert rel_l2(z[c], R @ r[c]) < 1e-10
+    z32 = vc.matvec(torch.tensor(r, device="cuda").float(), r_only=True).cpu().numpy()
+    for c in range(2):
+        assert rel_l2(z32[c], R @ r[c]) < 1e-5
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+@pytest.mark.parametrize("w", [SMALL[0], SMALL[1], SMALL[3], SMALL[4]], ids=lambda w: w.name)
+def test_capacitance_matches_oracle(w, precision):
+    ps = O.panels(w.labels, w.conductor_id, w.eps_r)
+    Cref, _, _ = O.capacitance(ps, voxel_size=w.voxel_size, rtol=1e-13)
+    vc = make(w, precision=precision)
+    C, st = vc.capacitance(tol=1e-8)
+    assert st["converged"] == 1
+    err = np.abs(C - Cref) / np.abs(Cref).max()
+    assert err.max() < 1e-6, (C, Cref)
+    assert np.all(np.abs(C - Cref) <= 1e-4 * np.abs(Cref) + 1e-9 * np.abs(Cref).max())
+
+
+def test_solve_residual_and_dense_solution():
+    import torch
+    w = SMALL[2]
+    ps = O.panels(w.labels, w.conductor_id, w.eps_r)
+    A = O.dense_matrix(ps, rtol=1e-14)
+    rng = np.random.default_rng(2)
+    B = rng.standard_normal((2, ps.n))
+    Xref = np.linalg.solve(A, B.T).T
+    for precision in ("fp64", "fp32_refine"):
+        vc = make(w, precision=precision)
+        X, st = vc.solve(torch.tensor(B, device="cuda"), tol=1e-10)
+        X = X.cpu().numpy()
+        for c in range(2):
+            assert np.linalg.norm(A @ X[c] - B[c]) <= 1e-9 * np.linalg.norm(B[c])
+            assert rel_l2(X[c], Xref[c]) < 1e-6
+        assert st["converged"] == 1
+
+
+def test_batched_structures_match_oracle():
+    """Several same-shape structures in one handle (one batch, shared
+    spectra) give each structure's own capacitance."""
+    boxes = W.small_boxes(6, 12, seed0=3)
+    labels = np.stack([b.labels for b in boxes])
+    V = _V()
+    vc = V.VoxCap(labels, boxes[0].conductor_id, boxes[0].eps_r, 1e-6)
+    Cs, st = vc.capacitance(tol=1e-8)
+    for b, C in zip(boxes, Cs):
+        ps = O.panels(b.labels, b.conductor_id, b.eps_r)
+        Cref, _, _ = O.capacitance(ps, voxel_size=1e-6, rtol=1e-12)
+        assert abs(C[0, 0] - Cref[0, 0]) <= 1e-6 * abs(Cref[0, 0])
