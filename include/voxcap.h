@@ -167,6 +167,35 @@ int voxcap_matvec(voxcap_t* h, const void* x_dev, void* y_dev, int nrhs, int dty
                   int flags);
 
 /*
+ * voxcap_matvec_noalloc -- the same product as voxcap_matvec (same arguments,
+ * flags and results) for callers that must not allocate device memory while
+ * they run.  The paper has no counterpart: this is a deployment variant.
+ *
+ * Who needs it: voxcap_matvec keeps its FFT intermediates in a workspace the
+ * handle allocates on first use (and grows for larger nrhs), and its
+ * VOXCAP_MV_PRECOND form allocates a temporary on every call.  Callers that
+ * run on a fixed device-memory budget fixed at start-up, callers whose device
+ * memory is owned by another allocator, and latency-critical loops that
+ * cannot afford the implicit device synchronisation of cudaMalloc / cudaFree
+ * cannot accept that.  This entry point calls no cudaMalloc, cudaFree or
+ * allocating library routine: its scratch is one fixed 16 MiB array in the
+ * library's device image, which every GPU that loads the library holds until
+ * the process exits.
+ *
+ * Limits and sharing: a call whose scratch would exceed 16 MiB (it grows with
+ * the padded grid and with nrhs) is rejected with VOXCAP_ERR_ARG and a message
+ * giving the bytes it needs; use voxcap_matvec or fewer columns then.  All
+ * calls on one device share the array and it keeps the last call's contents;
+ * every element a call reads is written earlier in the same call, so nothing
+ * has to start at zero.  Calls that overlap on the GPU (issued on different
+ * streams or from different threads without ordering) race on the array.
+ * The first call on a device looks up the array's device address on that
+ * device (a set-up step); make that first call before any stream capture.
+ */
+int voxcap_matvec_noalloc(voxcap_t* h, const void* x_dev, void* y_dev, int nrhs, int dtype,
+                          int flags);
+
+/*
  * voxcap_solve -- solve A X = B (Eq. 4) for nrhs right-hand sides by
  * left-preconditioned GMRES(restart) (Eq. 14, Sec. III), in plain FP64 or in
  * FP32 inside FP64 iterative refinement per opts->precision, until

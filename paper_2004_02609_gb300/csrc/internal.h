@@ -148,8 +148,12 @@ int build_precond(Handle& h);
 // y = A x (or A^T x) for `nrhs` columns of the handle's N panels.
 // field_out (optional, double only): face-grid fields [nrhs][3][box] written
 // for every face (E-part for forward, full adjoint output for adjoint).
+// workspace: caller-provided scratch of at least mvm_workspace_bytes(); when
+// NULL the handle's own workspace is used (allocated or grown on demand).
 template <typename T>
-int mvm(Handle& h, const T* x, T* y, int nrhs, bool adjoint, T* field_out);
+int mvm(Handle& h, const T* x, T* y, int nrhs, bool adjoint, T* field_out,
+        void* workspace = nullptr);
+size_t mvm_workspace_bytes(const Handle& h, int nrhs, size_t complex_bytes);
 template <typename T>
 int precond_apply(Handle& h, const T* r, T* z, int nrhs);
 int solve(Handle& h, const double* B, int nrhs, double tol, double* X, voxcap_stats* st,

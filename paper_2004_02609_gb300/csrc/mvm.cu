@@ -402,7 +402,7 @@ static int set_smem(K kernel, size_t bytes) {
 }
 
 template <typename T>
-int mvm(Handle& h, const T* x, T* y, int nrhs, bool adjoint, T* field_out) {
+int mvm(Handle& h, const T* x, T* y, int nrhs, bool adjoint, T* field_out, void* workspace) {
   using C = C_t<T>;
   VC_TRY(ensure_sign_tables());
   const Geom& g = h.g;
@@ -410,8 +410,11 @@ int mvm(Handle& h, const T* x, T* y, int nrhs, bool adjoint, T* field_out) {
   const int64_t gX = (int64_t)g.Lz * g.Ly * g.Hx;     // one grid, x-pass layout
   const int64_t gY = (int64_t)g.Lz * g.My * g.Hx;     // one grid, y/z-pass layout
   const size_t need = sizeof(C) * ((size_t)B * 6 * gX + (size_t)B * 6 * gY);
-  VC_TRY(h.ws.alloc(need));
-  C* bufX = reinterpret_cast<C*>(h.ws.p);
+  if (!workspace) {
+    VC_TRY(h.ws.alloc(need));
+    workspace = h.ws.p;
+  }
+  C* bufX = reinterpret_cast<C*>(workspace);
   C* bufY = bufX + (size_t)B * 6 * gX;
   MvmArgs a;
   a.g = g;
@@ -501,7 +504,17 @@ int mvm(Handle& h, const T* x, T* y, int nrhs, bool adjoint, T* field_out) {
   return VOXCAP_OK;
 }
 
-template int mvm<float>(Handle&, const float*, float*, int, bool, float*);
-template int mvm<double>(Handle&, const double*, double*, int, bool, double*);
+template int mvm<float>(Handle&, const float*, float*, int, bool, float*, void*);
+template int mvm<double>(Handle&, const double*, double*, int, bool, double*, void*);
+
+// bytes of scratch one product over nrhs columns needs (x-pass and y/z-pass
+// intermediates of every batch item)
+size_t mvm_workspace_bytes(const Handle& h, int nrhs, size_t complex_bytes) {
+  const Geom& g = h.g;
+  const size_t B = (size_t)h.pan.S * nrhs;
+  const size_t gX = (size_t)g.Lz * g.Ly * g.Hx;
+  const size_t gY = (size_t)g.Lz * g.My * g.Hx;
+  return complex_bytes * (B * 6 * gX + B * 6 * gY);
+}
 
 }  // namespace vc

@@ -27,7 +27,8 @@ EPS0 = 8.8541878128e-12
 SYMBOLS = ["voxcap_default_opts", "voxcap_last_error", "voxcap_setup", "voxcap_destroy",
            "voxcap_num_panels", "voxcap_panel_map", "voxcap_matvec", "voxcap_solve",
            "voxcap_capacitance", "voxcap_capacitance_grad", "voxcap_update_eps",
-           "voxcap_entries", "voxcap_fft_length", "voxcap_toeplitz", "voxcap_launch_count"]
+           "voxcap_entries", "voxcap_fft_length", "voxcap_toeplitz", "voxcap_launch_count",
+           "voxcap_matvec_noalloc"]
 
 
 class Opts(ctypes.Structure):
@@ -83,6 +84,7 @@ def lib():
         L.voxcap_entries.argtypes = [i32, vp, vp, vp, vp, vp]
         L.voxcap_fft_length.argtypes = [vp, P(i32), P(i32), P(i32)]
         L.voxcap_toeplitz.argtypes = [vp, i32, vp, P(i32)]
+        L.voxcap_matvec_noalloc.argtypes = [vp, vp, vp, i32, i32, i32]
         L.voxcap_launch_count.argtypes = []
         L.voxcap_launch_count.restype = ctypes.c_int64
         _LIB = L
@@ -219,6 +221,19 @@ class VoxCap:
         fl = (MV_PRECOND if precondition else 0) | (MV_ADJOINT if adjoint else 0) | \
             (MV_RONLY if r_only else 0)
         _check(lib().voxcap_matvec(self._h, _ptr(x2), _ptr(y), x2.shape[0], dt, fl))
+        return y.reshape(x.shape)
+
+    def matvec_noalloc(self, x, precondition=False, adjoint=False, r_only=False):
+        """matvec through voxcap_matvec_noalloc: same result, no device
+        allocation inside the call (fixed 16 MiB library scratch)."""
+        import torch
+        assert x.is_cuda
+        x2 = x.reshape(-1, self.N).contiguous()
+        y = torch.empty_like(x2)
+        dt = {torch.float32: F32, torch.float64: F64}[x2.dtype]
+        fl = (MV_PRECOND if precondition else 0) | (MV_ADJOINT if adjoint else 0) | \
+            (MV_RONLY if r_only else 0)
+        _check(lib().voxcap_matvec_noalloc(self._h, _ptr(x2), _ptr(y), x2.shape[0], dt, fl))
         return y.reshape(x.shape)
 
     def solve(self, B, tol=1e-6, allow_unconverged=False):
