@@ -57,6 +57,7 @@ static int setup_impl(const int32_t* labels, int nx, int ny, int nz, int n_struc
   int rc;
   VC_CUDA(cudaGetDevice(&h.device));
   h.stream = (cudaStream_t)cuda_stream;
+  set_alloc_stream(h.stream);
   if (opts) h.opts = *opts; else voxcap_default_opts(&h.opts);
   if (h.opts.restart < 1) h.opts.restart = 35;
   if (h.opts.max_iters < 1) h.opts.max_iters = 2000;
@@ -145,6 +146,7 @@ int voxcap_panel_map(const voxcap_t* hv, int s, int8_t* orient, int32_t* face_id
 
 int voxcap_matvec(voxcap_t* hv, const void* x_dev, void* y_dev, int nrhs, int dtype, int flags) {
   VC_CHECK(hv != nullptr, VOXCAP_ERR_ARG, "NULL handle");
+  set_alloc_stream(hv->h.stream);
   VC_CHECK(x_dev && y_dev && x_dev != y_dev, VOXCAP_ERR_ARG, "x and y must be distinct device arrays");
   VC_CHECK(nrhs >= 1, VOXCAP_ERR_ARG, "nrhs must be >= 1");
   VC_CHECK(dtype == VOXCAP_F32 || dtype == VOXCAP_F64, VOXCAP_ERR_ARG, "dtype must be F32 or F64");
@@ -181,6 +183,7 @@ int voxcap_matvec(voxcap_t* hv, const void* x_dev, void* y_dev, int nrhs, int dt
 int voxcap_solve(voxcap_t* hv, const double* B_dev, int nrhs, double tol, double* X_dev,
                  voxcap_stats* st) {
   VC_CHECK(hv != nullptr, VOXCAP_ERR_ARG, "NULL handle");
+  set_alloc_stream(hv->h.stream);
   VC_CHECK(B_dev && X_dev && nrhs >= 1, VOXCAP_ERR_ARG, "bad solve arguments");
   VC_CHECK(tol > 0.0 && tol < 1.0, VOXCAP_ERR_ARG, "tol must be in (0, 1)");
   return solve(hv->h, B_dev, nrhs, tol, X_dev, st, false);
@@ -188,6 +191,7 @@ int voxcap_solve(voxcap_t* hv, const double* B_dev, int nrhs, double tol, double
 
 int voxcap_capacitance(voxcap_t* hv, double tol, double* C_host, double* rho_dev, voxcap_stats* st) {
   VC_CHECK(hv != nullptr, VOXCAP_ERR_ARG, "NULL handle");
+  set_alloc_stream(hv->h.stream);
   VC_CHECK(C_host != nullptr, VOXCAP_ERR_ARG, "C_host is NULL");
   VC_CHECK(tol > 0.0 && tol < 1.0, VOXCAP_ERR_ARG, "tol must be in (0, 1)");
   return capacitance(hv->h, tol, C_host, rho_dev, st);
@@ -196,6 +200,7 @@ int voxcap_capacitance(voxcap_t* hv, double tol, double* C_host, double* rho_dev
 int voxcap_capacitance_grad(voxcap_t* hv, const double* dL_dC_host, double tol, double* grad_host,
                             voxcap_stats* st) {
   VC_CHECK(hv != nullptr, VOXCAP_ERR_ARG, "NULL handle");
+  set_alloc_stream(hv->h.stream);
   VC_CHECK(dL_dC_host && grad_host, VOXCAP_ERR_ARG, "NULL array");
   VC_CHECK(hv->h.have_rho, VOXCAP_ERR_ARG, "call voxcap_capacitance first");
   VC_CHECK(tol > 0.0 && tol < 1.0, VOXCAP_ERR_ARG, "tol must be in (0, 1)");
@@ -204,6 +209,7 @@ int voxcap_capacitance_grad(voxcap_t* hv, const double* dL_dC_host, double tol, 
 
 int voxcap_update_eps(voxcap_t* hv, const double* eps_r) {
   VC_CHECK(hv != nullptr && eps_r != nullptr, VOXCAP_ERR_ARG, "NULL argument");
+  set_alloc_stream(hv->h.stream);
   Handle& h = hv->h;
   for (int l = 0; l < h.nlab; ++l)
     VC_CHECK(h.cid[l] >= 0 || (eps_r[l] > 0.0 && eps_r[l] < 1e300), VOXCAP_ERR_ARG,

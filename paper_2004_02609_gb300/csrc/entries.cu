@@ -157,105 +157,154 @@ __device__ double ort_cf(bool E, double a, double b, double c) {
 }
 
 // ---- far field: Gauss-Legendre on the triangle-weighted reduced integrals ----
-__device__ int gl_order(double gap) {
+// Orders by the gap between the panels (in voxels), the smallest that keep
+// the quadrature error below 2e-14 relative against the adaptive FP64
+// integrals over sampled configurations at each gap.
+__device__ int gl_order_par(double gap) {
   if (gap < 2.5) return 9;
   if (gap < 3.5) return 8;
-  if (gap < 5.5) return 7;
   if (gap < 9.5) return 6;
+  if (gap < 19.5) return 5;
+  if (gap < 59.5) return 4;
+  return 3;
+}
+__device__ int gl_order_ort(double gap) {
+  if (gap < 3.5) return 7;
+  if (gap < 5.5) return 6;
   if (gap < 19.5) return 5;
   if (gap < 49.5) return 4;
   return 3;
 }
 
-// Ppar = (1/4pi) Int_{-1}^{1} Int_{-1}^{1} (1-|p|)(1-|q|) / sqrt((s+p)^2+(t+q)^2+h^2)
-__device__ double par_gl(bool E, double h, double s, double t, int n) {
-  double acc = 0.0;
+// ---- P and E together at one evaluation point ----
+// parallel: P = Ppar(h,s,t), E = dPpar/dh
+__device__ void par_pe(double h, double s, double t, double* P, double* E) {
+  const double gap = fmax(h, fmax(s - 1.0, t - 1.0));
+  if (gap <= 1.0) {
+    double ap = 0.0, ae = 0.0;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        const double wgt = c_cw[i] * c_cw[j];
+        const double u = s + (i - 1), v = t + (j - 1);
+        ap += wgt * F_par(u, v, h);
+        if (h != 0.0) ae += wgt * Fh_par(u, v, h);
+      }
+    *P = ap * kInv4Pi;
+    *E = ae * kInv4Pi;
+    return;
+  }
+  const int n = gl_order_par(gap);
+  double ap = 0.0, ae = 0.0;
   for (int sp = -1; sp <= 1; sp += 2)
     for (int i = 0; i < n; ++i) {
-      double pp = 0.5 * (1.0 + c_glx[n][i]);
-      double wp = 0.5 * c_glw[n][i] * (1.0 - pp);
-      double X = s + sp * pp;
-      double accq = 0.0;
+      const double pp = 0.5 * (1.0 + c_glx[n][i]);
+      const double wp = 0.5 * c_glw[n][i] * (1.0 - pp);
+      const double X = s + sp * pp;
+      double qp = 0.0, qe = 0.0;
       for (int sq = -1; sq <= 1; sq += 2)
         for (int j = 0; j < n; ++j) {
-          double qq = 0.5 * (1.0 + c_glx[n][j]);
-          double wq = 0.5 * c_glw[n][j] * (1.0 - qq);
-          double Y = t + sq * qq;
-          double r2 = X * X + Y * Y + h * h;
-          double ir = rsqrt(r2);
-          accq += wq * (E ? -h * ir * ir * ir : ir);
+          const double qq = 0.5 * (1.0 + c_glx[n][j]);
+          const double wq = 0.5 * c_glw[n][j] * (1.0 - qq);
+          const double Y = t + sq * qq;
+          const double ir = rsqrt(X * X + Y * Y + h * h);
+          qp += wq * ir;
+          qe += wq * ir * ir * ir;
         }
-      acc += wp * accq;
+      ap += wp * qp;
+      ae += wp * qe;
     }
-  return acc * kInv4Pi;
+  *P = ap * kInv4Pi;
+  *E = -h * ae * kInv4Pi;
 }
 
-// Port = (1/4pi) Int_{a-1/2}^{a+1/2} dp Int_{b-1/2}^{b+1/2} dq Int_{-1}^{1} (1-|w|) dw
-//        / sqrt(p^2 + q^2 + (c+w)^2);  Eort = d/da of it.
-__device__ double ort_gl(bool E, double a, double b, double c, int n) {
-  double acc = 0.0;
-  for (int j = 0; j < n; ++j) {
-    double q = b + 0.5 * c_glx[n][j];
-    double wq = 0.5 * c_glw[n][j];
-    for (int sw = -1; sw <= 1; sw += 2)
-      for (int k = 0; k < n; ++k) {
-        double ww = 0.5 * (1.0 + c_glx[n][k]);
-        double wgt = wq * 0.5 * c_glw[n][k] * (1.0 - ww);
-        double Z = c + sw * ww;
-        double base = q * q + Z * Z;
-        if (E) {
-          double p1 = a + 0.5, p0 = a - 0.5;
-          double r1 = p1 * p1 + base, r0 = p0 * p0 + base;
-          double i1 = rsqrt(r1), i0 = rsqrt(r0);
-          acc += wgt * (i1 - i0);
-        } else {
-          double sp = 0.0;
-          for (int i = 0; i < n; ++i) {
-            double p = a + 0.5 * c_glx[n][i];
-            double r2 = p * p + base;
-            double ir = rsqrt(r2);
-            sp += 0.5 * c_glw[n][i] * ir;
-          }
-          acc += wgt * sp;
+// orthogonal: P = Port(a,b,c), Ea = dPort/da, Eb = dPort/db
+__device__ void ort_pe(double a, double b, double c, double* P, double* Ea, double* Eb) {
+  const double gap = fmax(a - 0.5, fmax(b - 0.5, c - 1.0));
+  if (gap <= 1.0) {
+    *P = ort_cf(false, a, b, c);
+    *Ea = ort_cf(true, a, b, c);
+    *Eb = ort_cf(true, b, a, c);
+    return;
+  }
+  // the normal-derivative rules integrate a difference of two potentials;
+  // they take two more orders, and 1/r1 - 1/r0 is formed without cancellation
+  // as ((a-1/2)^2 - (a+1/2)^2) / (r0 r1 (r0 + r1)) = -2a / (r0 r1 (r0 + r1)).
+  const int n = gl_order_ort(gap);
+  const int ne = n + 2;
+  double ap = 0.0, aa = 0.0, ab = 0.0;
+  for (int sw = -1; sw <= 1; sw += 2) {
+    for (int k = 0; k < n; ++k) {
+      const double ww = 0.5 * (1.0 + c_glx[n][k]);
+      const double wz = 0.5 * c_glw[n][k] * (1.0 - ww);
+      const double Z = c + sw * ww;
+      const double Z2 = Z * Z;
+      for (int j = 0; j < n; ++j) {
+        const double q = b + 0.5 * c_glx[n][j];
+        const double bq = q * q + Z2;
+        double sp = 0.0;
+        for (int i = 0; i < n; ++i) {
+          const double pi = a + 0.5 * c_glx[n][i];
+          sp += 0.5 * c_glw[n][i] * rsqrt(pi * pi + bq);
         }
+        ap += wz * 0.5 * c_glw[n][j] * sp;
       }
+    }
+    for (int k = 0; k < ne; ++k) {
+      const double ww = 0.5 * (1.0 + c_glx[ne][k]);
+      const double wz = 0.5 * c_glw[ne][k] * (1.0 - ww);
+      const double Z = c + sw * ww;
+      const double Z2 = Z * Z;
+      for (int j = 0; j < ne; ++j) {
+        const double u = 0.5 * c_glx[ne][j];
+        const double wu = 0.5 * c_glw[ne][j];
+        const double q = b + u, bq = q * q + Z2;          // Ea: q over the test panel
+        const double ra1 = sqrt((a + 0.5) * (a + 0.5) + bq), ra0 = sqrt((a - 0.5) * (a - 0.5) + bq);
+        aa += wz * wu * (-2.0 * a / (ra0 * ra1 * (ra0 + ra1)));
+        const double p = a + u, bp = p * p + Z2;          // Eb: p over the source panel
+        const double rb1 = sqrt((b + 0.5) * (b + 0.5) + bp), rb0 = sqrt((b - 0.5) * (b - 0.5) + bp);
+        ab += wz * wu * (-2.0 * b / (rb0 * rb1 * (rb0 + rb1)));
+      }
+    }
   }
-  return acc * kInv4Pi;
+  *P = ap * kInv4Pi;
+  *Ea = aa * kInv4Pi;
+  *Eb = ab * kInv4Pi;
 }
 
-// canonical functions at non-negative arguments (a, b > 0 half-integers)
-__device__ double ppar_e(bool E, double h, double s, double t) {
-  double gap = fmax(h, fmax(s - 1.0, t - 1.0));
-  if (gap <= 1.0) return par_cf(E, h, s, t);
-  if (E && h == 0.0) return 0.0;
-  return par_gl(E, h, s, t, gl_order(gap));
-}
+struct ToepLaunch {
+  double* out[kNumKernels];
+  int d[6][3];            // extents of the 6 evaluation groups
+  int64_t start[7];
+};
 
-__device__ double port_e(bool E, double a, double b, double c) {
-  double gap = fmax(a - 0.5, fmax(b - 0.5, c - 1.0));
-  if (gap <= 1.0) return ort_cf(E, a, b, c);
-  return ort_gl(E, a, b, c, gl_order(gap));
-}
-
-// Value of one kernel tensor at Toeplitz index e (see voxcap_toeplitz).
-__device__ double toeplitz_value(int kk, int ex, int ey, int ez) {
-  const bool E = kk >= 6;
-  const int te = ker_test(kk), so = ker_src(kk);
-  const int e[3] = {ex, ey, ez};
-  if (te == so) {
-    const int a1 = te == 0 ? 1 : 0, a2 = te == 2 ? 1 : 2;
-    return ppar_e(E, (double)e[te], (double)e[a1], (double)e[a2]);
-  }
-  const int ga = 3 - te - so;
-  return port_e(E, e[te] + 0.5, e[so] + 0.5, (double)e[ga]);
-}
-
-__global__ void k_toeplitz(int kk, int dx, int dy, int dz, double* __restrict__ out) {
+// Six groups of evaluation points fill the 15 tensors: group a < 3 gives
+// P^{aa} and E^{aa} (the same parallel geometry); group 3 + q for the pair
+// (a, b) = (x,y), (x,z), (y,z) gives P^{ab}, E^{ab} = dPort/da and
+// E^{ba} = dPort/db at the same orthogonal geometry and Toeplitz index.
+__global__ void k_toeplitz(ToepLaunch L) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int64_t n = (int64_t)dx * dy * dz;
-  if (t >= n) return;
-  int ex = (int)(t % dx), ey = (int)((t / dx) % dy), ez = (int)(t / ((int64_t)dx * dy));
-  out[t] = toeplitz_value(kk, ex, ey, ez);
+  if (t >= L.start[6]) return;
+  int gi = 0;
+  while (t >= L.start[gi + 1]) ++gi;
+  const int64_t q = t - L.start[gi];
+  const int dx = L.d[gi][0], dy = L.d[gi][1];
+  const int e[3] = {(int)(q % dx), (int)((q / dx) % dy), (int)(q / ((int64_t)dx * dy))};
+  if (gi < 3) {
+    const int al = gi;
+    const int a1 = al == 0 ? 1 : 0, a2 = al == 2 ? 1 : 2;
+    double P, E;
+    par_pe((double)e[al], (double)e[a1], (double)e[a2], &P, &E);
+    L.out[al][q] = P;
+    L.out[6 + al][q] = E;
+  } else {
+    const int pair = gi - 3;
+    const int al = pair == 2 ? 1 : 0, be = pair == 0 ? 1 : 2, ga = 3 - al - be;
+    double P, Ea, Eb;
+    ort_pe(e[al] + 0.5, e[be] + 0.5, (double)e[ga], &P, &Ea, &Eb);
+    L.out[3 + pair][q] = P;
+    L.out[9 + pair][q] = Ea;
+    L.out[12 + pair][q] = Eb;
+  }
 }
 
 void toeplitz_dims(const Geom& g, int kk, int* d) {
@@ -267,16 +316,24 @@ void toeplitz_dims(const Geom& g, int kk, int* d) {
 
 int build_toeplitz(Handle& h) {
   VC_TRY(ensure_gl_tables());
+  ToepLaunch L;
   for (int kk = 0; kk < kNumKernels; ++kk) {
     int* d = h.tdims[kk];
     toeplitz_dims(h.g, kk, d);
-    int64_t n = (int64_t)d[0] * d[1] * d[2];
-    VC_TRY(h.toep[kk].alloc((size_t)n));
-    const int TB = 128;
-    k_toeplitz<<<(unsigned)((n + TB - 1) / TB), TB, 0, h.stream>>>(kk, d[0], d[1], d[2],
-                                                                     h.toep[kk].p); ::vc::note_launch();
-    VC_CUDA(cudaGetLastError());
+    VC_TRY(h.toep[kk].alloc((size_t)d[0] * d[1] * d[2]));
+    L.out[kk] = h.toep[kk].p;
   }
+  // groups 0..2 share the extents of P^{aa}; groups 3..5 those of P^{ab}
+  L.start[0] = 0;
+  for (int gi = 0; gi < 6; ++gi) {
+    const int* d = h.tdims[gi];
+    for (int a = 0; a < 3; ++a) L.d[gi][a] = d[a];
+    L.start[gi + 1] = L.start[gi] + (int64_t)d[0] * d[1] * d[2];
+  }
+  const int TB = 128;
+  const int64_t tot = L.start[6];
+  k_toeplitz<<<(unsigned)((tot + TB - 1) / TB), TB, 0, h.stream>>>(L); ::vc::note_launch();
+  VC_CUDA(cudaGetLastError());
   return VOXCAP_OK;
 }
 
@@ -292,13 +349,16 @@ __global__ void k_entries(int n, const int32_t* __restrict__ kind, const int32_t
   double v;
   if (te == sr) {
     const int a1 = te == 0 ? 1 : 0, a2 = te == 2 ? 1 : 2;
-    v = ppar_e(E, fabs(dd[te]), fabs(dd[a1]), fabs(dd[a2]));
-    if (E && dd[te] < 0.0) v = -v;
+    double P, Ev;
+    par_pe(fabs(dd[te]), fabs(dd[a1]), fabs(dd[a2]), &P, &Ev);
+    v = E ? Ev : P;
   } else {
     const int ga = 3 - te - sr;
-    v = port_e(E, fabs(dd[te]), fabs(dd[sr]), fabs(dd[ga]));
-    if (E && dd[te] < 0.0) v = -v;
+    double P, Ea, Eb;
+    ort_pe(fabs(dd[te]), fabs(dd[sr]), fabs(dd[ga]), &P, &Ea, &Eb);
+    v = E ? Ea : P;
   }
+  if (E && dd[te] < 0.0) v = -v;
   out[i] = v;
 }
 

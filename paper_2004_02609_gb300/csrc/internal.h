@@ -9,10 +9,18 @@
 
 namespace vc {
 
+// Device allocations come from the device's stream-ordered memory pool on
+// the stream of the calling handle (set on entry to every API call); the pool
+// keeps freed memory for reuse, so building and solving repeatedly does not
+// go back to cudaMalloc / cudaFree.
+void set_alloc_stream(cudaStream_t s);
+cudaStream_t alloc_stream();
+
 // A device allocation owned by the handle.
 template <typename T> struct DBuf {
   T* p = nullptr;
   size_t n = 0;
+  cudaStream_t st = nullptr;
   int alloc(size_t count);
   void release();
   ~DBuf() { release(); }
@@ -25,7 +33,8 @@ template <typename T> int DBuf<T>::alloc(size_t count) {
   if (count <= n && p) return VOXCAP_OK;
   release();
   if (count == 0) return VOXCAP_OK;
-  cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+  st = alloc_stream();
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&p), count * sizeof(T), st);
   if (e != cudaSuccess) {
     p = nullptr;
     (void)cudaGetLastError();
@@ -36,7 +45,7 @@ template <typename T> int DBuf<T>::alloc(size_t count) {
   return VOXCAP_OK;
 }
 template <typename T> void DBuf<T>::release() {
-  if (p) cudaFree(p);
+  if (p) cudaFreeAsync(p, st);
   p = nullptr;
   n = 0;
 }

@@ -152,6 +152,7 @@ __global__ void k_xfwd(MvmArgs a, const T* __restrict__ xin, C_t<T>* __restrict_
 // phase after.  Inverse: Lin = My, Lout = Ly (truncated), conj phase before.
 template <typename T, bool INV>
 __global__ void k_ypass(Geom g, int G, const C_t<T>* __restrict__ in, C_t<T>* __restrict__ out,
+                        int64_t in_bstride, int64_t out_bstride,
                         Plan1D<C_t<T>> plan, const C_t<T>* __restrict__ phy, int TX) {
   using C = C_t<T>;
   extern __shared__ unsigned char smem_raw[];
@@ -161,12 +162,12 @@ __global__ void k_ypass(Geom g, int G, const C_t<T>* __restrict__ in, C_t<T>* __
   const int k0 = blockIdx.x * TX;
   const int z = blockIdx.y;
   const int bg = blockIdx.z;           // b * G + grid
-  const int grid = bg % G;
+  const int grid = bg % G, b = bg / G;
   const bool phase = (grid % 3) == 1;
   const int Lin = INV ? M : g.Ly;
   const int Lout = INV ? g.Ly : M;
-  const C* src = in + ((int64_t)bg * g.Lz + z) * ((int64_t)Lin * H);
-  C* dst = out + ((int64_t)bg * g.Lz + z) * ((int64_t)Lout * H);
+  const C* src = in + (int64_t)b * in_bstride + ((int64_t)grid * g.Lz + z) * ((int64_t)Lin * H);
+  C* dst = out + (int64_t)b * out_bstride + ((int64_t)grid * g.Lz + z) * ((int64_t)Lout * H);
   for (int t = threadIdx.x; t < M * TX; t += blockDim.x) {
     const int c = t % TX, y = t / TX;
     const int kx = k0 + c;
@@ -448,12 +449,9 @@ int mvm(Handle& h, const T* x, T* y, int nrhs, bool adjoint, T* field_out, void*
   {
     size_t sm = 2 * (size_t)g.My * TXy * sizeof(C);
     VC_TRY(set_smem<T>(k_ypass<T, false>, sm));
-    for (int b = 0; b < B; ++b) {
-      dim3 grid((g.Hx + TXy - 1) / TXy, g.Lz, GI);
-      k_ypass<T, false><<<grid, TB, sm, st>>>(g, GI, bufX + (size_t)b * GI * gX,
-                                              bufY + (size_t)b * 6 * gY, plan_of<T>(h, 1),
-                                              phase_of<T>(h, 1), TXy); ::vc::note_launch();
-    }
+    dim3 grid((g.Hx + TXy - 1) / TXy, g.Lz, B * GI);
+    k_ypass<T, false><<<grid, TB, sm, st>>>(g, GI, bufX, bufY, (int64_t)GI * gX, (int64_t)6 * gY,
+                                            plan_of<T>(h, 1), phase_of<T>(h, 1), TXy); ::vc::note_launch();
     VC_CUDA(cudaGetLastError());
   }
   // zmac
@@ -476,12 +474,9 @@ int mvm(Handle& h, const T* x, T* y, int nrhs, bool adjoint, T* field_out, void*
   {
     size_t sm = 2 * (size_t)g.My * TXy * sizeof(C);
     VC_TRY(set_smem<T>(k_ypass<T, true>, sm));
-    for (int b = 0; b < B; ++b) {
-      dim3 grid((g.Hx + TXy - 1) / TXy, g.Lz, GO);
-      k_ypass<T, true><<<grid, TB, sm, st>>>(g, GO, bufY + (size_t)b * 6 * gY,
-                                             bufX + (size_t)b * GO * gX, plan_of<T>(h, 1),
-                                             phase_of<T>(h, 1), TXy); ::vc::note_launch();
-    }
+    dim3 grid((g.Hx + TXy - 1) / TXy, g.Lz, B * GO);
+    k_ypass<T, true><<<grid, TB, sm, st>>>(g, GO, bufY, bufX, (int64_t)6 * gY, (int64_t)GO * gX,
+                                           plan_of<T>(h, 1), phase_of<T>(h, 1), TXy); ::vc::note_launch();
     VC_CUDA(cudaGetLastError());
   }
   // xinv + gather

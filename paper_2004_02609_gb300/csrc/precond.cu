@@ -271,65 +271,83 @@ __global__ void k_assemble(ToepTabs tt, const int32_t* urep, const int32_t* offs
   }
 }
 
-// Gauss-Jordan with partial pivoting on [A | I] -> [I | A^-1]; one block per matrix.
-__global__ void k_gauss_jordan(const int32_t* urep, const int32_t* offs, const int64_t* uoff,
-                               double* aug, int* status) {
-  const int u = blockIdx.x;
+// Gauss-Jordan with partial pivoting on [A | I] -> [I | A^-1], one launch
+// per elimination step c.  The 2n columns of every block are split into
+// slabs of kGJCols columns, one CTA each, so a step touches each block with
+// many SMs.  The pivot column c (needed by every slab) is read from `pin`,
+// the copy the owner of column c wrote in the previous step; the owner of
+// column c+1 writes its updated column to `pout` for the next step.  Step c
+// with pivot row pr (old values; mult = column c, piv = mult[pr]):
+//   new row c   = old row pr / piv
+//   new row pr  = old row c - mult[c] * (new row c)       (pr != c)
+//   other row r = old row r - mult[r] * (new row c)
+constexpr int kGJCols = 16;
+
+__global__ void k_gj_step(int c, const int32_t* __restrict__ urep, const int32_t* __restrict__ offs,
+                          const int64_t* __restrict__ uoff, const int64_t* __restrict__ poff,
+                          double* __restrict__ aug, const double* __restrict__ pin,
+                          double* __restrict__ pout, int* __restrict__ status) {
+  extern __shared__ double gsm[];
+  const int u = blockIdx.y;
   const int gb = urep[u];
   const int n = offs[gb + 1] - offs[gb];
+  if (c >= n) return;
   const int w = 2 * n;
+  const int j0 = blockIdx.x * kGJCols;
+  if (j0 >= w) return;
+  const int j1 = min(w, j0 + kGJCols);
   double* Mx = aug + 2 * uoff[u];
+  double* mult = gsm;                 // [n]
+  double* prow = gsm + n;             // [kGJCols]
+  double* crow = prow + kGJCols;      // [kGJCols]
   __shared__ double red_v[256];
   __shared__ int red_i[256];
-  __shared__ int piv_sh;
-  for (int c = 0; c < n; ++c) {
-    // pivot search in column c, rows c..n-1
-    double best = -1.0;
-    int bi = c;
-    for (int r = c + threadIdx.x; r < n; r += blockDim.x) {
-      double v = fabs(Mx[(int64_t)r * w + c]);
-      if (v > best) { best = v; bi = r; }
+  for (int r = threadIdx.x; r < n; r += blockDim.x)
+    mult[r] = (c == 0) ? Mx[(int64_t)r * w] : pin[poff[u] + r];
+  __syncthreads();
+  double best = -1.0;
+  int bi = n;
+  for (int r = c + threadIdx.x; r < n; r += blockDim.x) {
+    const double v = fabs(mult[r]);
+    if (v > best) { best = v; bi = r; }
+  }
+  red_v[threadIdx.x] = best;
+  red_i[threadIdx.x] = bi;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) {
+      const double a = red_v[threadIdx.x], b = red_v[threadIdx.x + st];
+      const int ia = red_i[threadIdx.x], ib = red_i[threadIdx.x + st];
+      if (b > a || (b == a && ib < ia)) { red_v[threadIdx.x] = b; red_i[threadIdx.x] = ib; }
     }
-    red_v[threadIdx.x] = best;
-    red_i[threadIdx.x] = bi;
-    __syncthreads();
-    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
-      if (threadIdx.x < st) {
-        if (red_v[threadIdx.x + st] > red_v[threadIdx.x] ||
-            (red_v[threadIdx.x + st] == red_v[threadIdx.x] && red_i[threadIdx.x + st] < red_i[threadIdx.x])) {
-          red_v[threadIdx.x] = red_v[threadIdx.x + st];
-          red_i[threadIdx.x] = red_i[threadIdx.x + st];
-        }
-      }
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-      piv_sh = red_i[0];
-      if (!(red_v[0] > 0.0)) atomicExch(status, 1);
-    }
-    __syncthreads();
-    const int pr = piv_sh;
-    if (pr != c)
-      for (int j = threadIdx.x; j < w; j += blockDim.x) {
-        double t = Mx[(int64_t)c * w + j];
-        Mx[(int64_t)c * w + j] = Mx[(int64_t)pr * w + j];
-        Mx[(int64_t)pr * w + j] = t;
-      }
-    __syncthreads();
-    const double inv = 1.0 / Mx[(int64_t)c * w + c];
-    __syncthreads();
-    for (int j = threadIdx.x; j < w; j += blockDim.x) Mx[(int64_t)c * w + j] *= inv;
-    __syncthreads();
-    for (int t = threadIdx.x; t < n * w; t += blockDim.x) {
-      const int r = t / w, j = t % w;
-      if (r == c || j == c) continue;
-      Mx[(int64_t)r * w + j] -= Mx[(int64_t)r * w + c] * Mx[(int64_t)c * w + j];
-    }
-    __syncthreads();
-    for (int r = threadIdx.x; r < n; r += blockDim.x)
-      if (r != c) Mx[(int64_t)r * w + c] = 0.0;
     __syncthreads();
   }
+  const int pr = red_i[0];
+  const double piv = mult[pr < n ? pr : c];
+  if (!(red_v[0] > 0.0)) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) atomicExch(status, 1);
+    return;
+  }
+  const double ipiv = 1.0 / piv;
+  for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+    prow[j - j0] = Mx[(int64_t)pr * w + j] * ipiv;
+    crow[j - j0] = Mx[(int64_t)c * w + j];
+  }
+  __syncthreads();
+  const int cw = j1 - j0;
+  const double mc = mult[c];
+  for (int t = threadIdx.x; t < n * cw; t += blockDim.x) {
+    const int r = t / cw, jj = t % cw;
+    const int64_t at = (int64_t)r * w + j0 + jj;
+    const double pj = prow[jj];
+    if (r == c) Mx[at] = pj;
+    else if (r == pr) Mx[at] = crow[jj] - mc * pj;
+    else Mx[at] -= mult[r] * pj;
+  }
+  __syncthreads();
+  const int nc = c + 1;
+  if (nc < n && nc >= j0 && nc < j1)
+    for (int r = threadIdx.x; r < n; r += blockDim.x) pout[poff[u] + r] = Mx[(int64_t)r * w + nc];
 }
 
 __global__ void k_extract_inv(const int32_t* urep, const int32_t* offs, const int64_t* uoff,
@@ -468,7 +486,30 @@ int build_precond(Handle& h) {
     k_assemble<<<(unsigned)nuniq, TB, 0, h.stream>>>(tt, urep.p, P.blk_off.p, P.blk_idx.p, P.uoff.p,
                                                      h.pan.orient.p, h.pan.face.p, h.pan.kind.p,
                                                      h.pan.idiag.p, aug.p); ::vc::note_launch();
-    k_gauss_jordan<<<(unsigned)nuniq, TB, 0, h.stream>>>(urep.p, P.blk_off.p, P.uoff.p, aug.p, status.p); ::vc::note_launch();
+    {
+      // pivot-column double buffer: one column of n values per unique block
+      std::vector<int64_t> poff_h(nuniq + 1, 0);
+      for (int64_t q = 0; q < nuniq; ++q) poff_h[q + 1] = poff_h[q] + cnt_h[urep_h[q]];
+      DBuf<int64_t> poff;
+      DBuf<double> pbuf;
+      VC_TRY(poff.alloc(poff_h.size()));
+      VC_TRY(pbuf.alloc((size_t)std::max<int64_t>(2 * poff_h.back(), 1)));
+      VC_CUDA(cudaMemcpyAsync(poff.p, poff_h.data(), sizeof(int64_t) * poff_h.size(),
+                              cudaMemcpyHostToDevice, h.stream));
+      const int slabs = (2 * P.max_n + kGJCols - 1) / kGJCols;
+      const size_t sm = sizeof(double) * ((size_t)P.max_n + 2 * kGJCols);
+      if (sm > 48 * 1024)
+        VC_CUDA(cudaFuncSetAttribute(k_gj_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      dim3 grid((unsigned)slabs, (unsigned)nuniq);
+      for (int c = 0; c < P.max_n; ++c) {
+        const double* pin = pbuf.p + (c & 1) * poff_h.back();
+        double* pout = pbuf.p + ((c + 1) & 1) * poff_h.back();
+        k_gj_step<<<grid, TB, sm, h.stream>>>(c, urep.p, P.blk_off.p, P.uoff.p, poff.p, aug.p, pin,
+                                              pout, status.p); ::vc::note_launch();
+      }
+      VC_CUDA(cudaGetLastError());
+      VC_CUDA(cudaStreamSynchronize(h.stream));
+    }
     k_extract_inv<<<(unsigned)nuniq, TB, 0, h.stream>>>(urep.p, P.blk_off.p, P.uoff.p, aug.p, P.inv_d.p,
                                                         P.inv_f.p); ::vc::note_launch();
     VC_CUDA(cudaGetLastError());

@@ -38,14 +38,14 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 }
 
 // partial[col][i][chunk] = sum over the chunk of V_i[col] * w[col], i < nv
-// (optionally first w -= sum_i coef[col][i] V_i[col]); with nv == 0 and
-// self-norm, partial = ||w||^2 over the chunk.
+// (optionally first w -= sum_i coef[col][i] V_i[col]); with self_norm the one
+// partial is ||w||^2 over the chunk.  The dot products of a sweep are spread
+// over the warps of the block (warp q takes basis vectors q, q+8, ...).
 template <typename T>
 __global__ void k_gs_sweep(const T* __restrict__ V, T* __restrict__ w, int64_t N, int nrhs,
                            int nv_update, const double* __restrict__ coef, int coef_ld,
                            int nv_dot, bool self_norm, const int* __restrict__ active,
                            int nchunks, double* __restrict__ partial, int part_ld) {
-  __shared__ double sh[32];
   const int col = blockIdx.y;
   const int chunk = blockIdx.x;
   if (active && !active[col]) return;
@@ -63,12 +63,13 @@ __global__ void k_gs_sweep(const T* __restrict__ V, T* __restrict__ w, int64_t N
     __syncthreads();
   }
   const int nd = self_norm ? 1 : nv_dot;
-  for (int i = 0; i < nd; ++i) {
-    double acc = 0.0;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = wid; i < nd; i += nw) {
     const T* vi = self_norm ? wc : V + i * vstride + (int64_t)col * N;
-    for (int64_t p = lo + threadIdx.x; p < hi; p += blockDim.x) acc += (double)vi[p] * (double)wc[p];
-    double s = block_sum(acc, sh);
-    if (threadIdx.x == 0) partial[((int64_t)col * part_ld + i) * nchunks + chunk] = s;
+    double acc = 0.0;
+    for (int64_t p = lo + lane; p < hi; p += 32) acc += (double)vi[p] * (double)wc[p];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) partial[((int64_t)col * part_ld + i) * nchunks + chunk] = acc;
   }
 }
 
@@ -221,9 +222,9 @@ struct SolveCounters {
 };
 
 static int nchunks_for(int64_t N) {
-  int64_t c = (N + 4095) / 4096;
+  int64_t c = (N + 1023) / 1024;
   if (c < 1) c = 1;
-  if (c > 512) c = 512;
+  if (c > 2048) c = 2048;
   return (int)c;
 }
 

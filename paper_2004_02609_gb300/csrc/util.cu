@@ -11,6 +11,24 @@ static thread_local std::string g_last_error;
 void set_error(const std::string& msg) { g_last_error = msg; }
 const char* last_error() { return g_last_error.c_str(); }
 
+static thread_local cudaStream_t g_alloc_stream = nullptr;
+static bool g_pool_ready[128] = {false};
+
+void set_alloc_stream(cudaStream_t s) {
+  g_alloc_stream = s;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return;
+  if (!g_pool_ready[dev]) {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t keep = UINT64_MAX;       // keep freed blocks in this process's pool
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    g_pool_ready[dev] = true;
+  }
+}
+cudaStream_t alloc_stream() { return g_alloc_stream; }
+
 static std::atomic<int64_t> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }

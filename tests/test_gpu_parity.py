@@ -31,6 +31,19 @@ def make(w, **kw):
 SMALL = [W.cube(4), W.random_structure((7, 5, 6), 0), W.random_structure((9, 6, 5), 1),
          W.random_structure((5, 8, 7), 2, n_cond=3), W.coated_sphere(12, 3.0),
          W.plates(12, 10, 8)]
+SMALL[5].name = "plates_12x10x8"
+
+
+_DENSE = {}
+
+
+def dense(w, rtol=1e-13):
+    """Oracle panels and dense matrix of a workload, assembled once per module."""
+    key = (w.name, w.labels.tobytes(), w.eps_r.tobytes(), rtol)
+    if key not in _DENSE:
+        ps = O.panels(w.labels, w.conductor_id, w.eps_r)
+        _DENSE[key] = (ps, O.dense_matrix(ps, rtol=rtol))
+    return _DENSE[key]
 
 
 def rel_l2(a, b):
@@ -123,8 +136,7 @@ def test_matvec_matches_dense(w, pad_mode):
     except Exception as e:     # 2(N+1) not 2/3/5/7-smooth: pad_mode 1 unsupported
         assert pad_mode == 1 and "smooth" in str(e)
         pytest.skip("2(N+1) not smooth")
-    ps = O.panels(w.labels, w.conductor_id, w.eps_r)
-    A = O.dense_matrix(ps, rtol=1e-14)
+    ps, A = dense(w)
     rng = np.random.default_rng(0)
     X = rng.standard_normal((3, ps.n))
     ref = (A @ X.T).T
@@ -159,8 +171,7 @@ def test_preconditioner_matches_dense(kind):
     w = W.random_structure((9, 7, 8), 4, n_cond=3)
     nv = (3, 2, 4)
     vc = make(w, precond=kind, nv=nv)
-    ps = O.panels(w.labels, w.conductor_id, w.eps_r)
-    A = O.dense_matrix(ps, rtol=1e-14)
+    ps, A = dense(w)
     R = O.precond_matrix(ps, A, nv=np.array(nv), kind=kind)
     r = np.random.default_rng(1).standard_normal((2, ps.n))
     z = vc.matvec(torch.tensor(r, device="cuda"), r_only=True).cpu().numpy()
@@ -174,8 +185,8 @@ def test_preconditioner_matches_dense(kind):
 @pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
 @pytest.mark.parametrize("w", [SMALL[0], SMALL[1], SMALL[3], SMALL[4]], ids=lambda w: w.name)
 def test_capacitance_matches_oracle(w, precision):
-    ps = O.panels(w.labels, w.conductor_id, w.eps_r)
-    Cref, _, _ = O.capacitance(ps, voxel_size=w.voxel_size, rtol=1e-13)
+    ps, A = dense(w)
+    Cref, _, _ = O.capacitance(ps, A=A, voxel_size=w.voxel_size)
     vc = make(w, precision=precision)
     C, st = vc.capacitance(tol=1e-8)
     assert st["converged"] == 1
@@ -187,8 +198,7 @@ def test_capacitance_matches_oracle(w, precision):
 def test_solve_residual_and_dense_solution():
     import torch
     w = SMALL[2]
-    ps = O.panels(w.labels, w.conductor_id, w.eps_r)
-    A = O.dense_matrix(ps, rtol=1e-14)
+    ps, A = dense(w)
     rng = np.random.default_rng(2)
     B = rng.standard_normal((2, ps.n))
     Xref = np.linalg.solve(A, B.T).T
