@@ -74,6 +74,26 @@ extern "C" {
 
 typedef struct voxcap voxcap_t;
 
+/*
+ * voxcap_tucker -- Tucker-compressed canonical Toeplitz tensors (Eq. 13,
+ * Sec. II.C), produced once at installation (paper_2004_02609_gb300/tucker.py)
+ * in normalised units.  Tensor t:
+ *   0  Ppar[h][s][t]  potential of parallel panels, offsets (h, s, t)
+ *   1  Epar[h][s][t]  its derivative along the normal offset h
+ *   2  Port[a][b][c]  potential of orthogonal panels at offsets
+ *                     (a + 1/2, b + 1/2, c): test normal, source normal, shared axis
+ *   3  Eort[a][b][c]  its derivative along the test normal
+ * X ~ core x1 U1 x2 U2 x3 U3 with core[r1][r2][r3] (last index fastest) and
+ * factor[t][n] a dims[t][n] x ranks[t][n] row-major matrix; all host memory,
+ * copied during voxcap_setup.  Every dims[t][n] must be >= max(nx, ny, nz) + 1.
+ */
+typedef struct voxcap_tucker {
+  int dims[4][3];
+  int ranks[4][3];
+  const double* core[4];
+  const double* factor[4][3];
+} voxcap_tucker;
+
 typedef struct voxcap_opts {
   int precision;       /* VOXCAP_FP64 or VOXCAP_FP32_REFINE (default) */
   int restart;         /* GMRES restart length (default 35, Sec. III) */
@@ -84,7 +104,9 @@ typedef struct voxcap_opts {
   int precond;         /* VOXCAP_PRECOND_* (default BDD) */
   int pad_mode;        /* 0: smallest even 2/3/5/7-smooth M >= 2N+1 per axis (default);
                           1: the paper's M = 2(N+1) (must be 2/3/5/7-smooth) */
-  int use_tucker;      /* 1: Toeplitz tensors from Tucker factors (voxcap_setup_tucker) */
+  const voxcap_tucker* tucker; /* NULL: generate the Toeplitz tensors in FP64 (Eqs. 5-6);
+                          else restore them from these Tucker factors on the
+                          tensor cores (Sec. II.C), cropped to the grid */
 } voxcap_opts;
 
 typedef struct voxcap_stats {
@@ -255,6 +277,26 @@ int voxcap_update_eps(voxcap_t* h, const double* eps_r);
  */
 int voxcap_entries(int n, const int32_t* kind, const int32_t* test_orient,
                    const int32_t* src_orient, const double* d, double* out);
+
+/*
+ * voxcap_tucker_expand -- X = S x1 U1 x2 U2 x3 U3 (Eq. 13) on the tensor cores
+ * (tcgen05, TF32 hi/lo split, FP32 accumulation): the restoration step of
+ * Sec. II.C.  Device arrays: core [r1][r2][r3] (last index fastest),
+ * U1 [D1][r1], U2 [D2][r2], U3 [D3][r3] row-major, out [D3][D2][D1] (first
+ * index fastest: out[i + D1 (j + D2 k)]).  Legacy default stream; synchronises.
+ * Returns VOXCAP_ERR_CUDA if the tensor cores do not complete within a bound.
+ */
+int voxcap_tucker_expand(const double* core, int r1, int r2, int r3, const double* U1, int D1,
+                         const double* U2, int D2, const double* U3, int D3, double* out);
+
+/*
+ * voxcap_canonical_tensors -- the four canonical Toeplitz tensors of
+ * voxcap_tucker on a D x D x D index cube, generated in FP64 on the device
+ * (Eqs. 5-6, Appendix A-B): the installation-stage input of the Tucker
+ * compression.  Each output is device double [D][D][D] (first index fastest);
+ * any pointer may be NULL.  Legacy default stream; synchronises.
+ */
+int voxcap_canonical_tensors(int D, double* ppar, double* epar, double* port, double* eort);
 
 /*
  * voxcap_fft_length -- the padded FFT length the handle uses along each axis

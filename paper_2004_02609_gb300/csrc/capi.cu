@@ -9,6 +9,8 @@
 namespace vc {
 const char* last_error();
 void toeplitz_dims(const Geom& g, int kk, int* d);
+int build_toeplitz_tucker(Handle& h, const voxcap_tucker& tk);
+int canonical_tensors(int D, double* ppar, double* epar, double* port, double* eort);
 }
 
 struct voxcap {
@@ -29,7 +31,7 @@ void voxcap_default_opts(voxcap_opts* o) {
   o->nv[0] = o->nv[1] = o->nv[2] = 10;
   o->precond = VOXCAP_PRECOND_BDD;
   o->pad_mode = 0;
-  o->use_tucker = 0;
+  o->tucker = nullptr;
 }
 
 const char* voxcap_last_error(void) { return vc::last_error(); }
@@ -88,7 +90,12 @@ static int setup_impl(const int32_t* labels, int nx, int ny, int nz, int n_struc
   }
   if ((rc = build_fft_plans(h))) return fail(rc);
   if ((rc = build_panels(h))) return fail(rc);
-  if ((rc = build_toeplitz(h))) return fail(rc);
+  if (h.opts.tucker) {
+    if ((rc = build_toeplitz_tucker(h, *h.opts.tucker))) return fail(rc);
+  } else if ((rc = build_toeplitz(h))) {
+    return fail(rc);
+  }
+  h.opts.tucker = nullptr;        // the caller's factors are not retained
   if ((rc = build_spectra(h))) return fail(rc);
   if ((rc = build_precond(h))) return fail(rc);
   *out = v;
@@ -228,6 +235,11 @@ int voxcap_entries(int n, const int32_t* kind, const int32_t* test_orient, const
   if (n == 0) return VOXCAP_OK;
   VC_CHECK(kind && test_orient && src_orient && d && out, VOXCAP_ERR_ARG, "NULL array");
   return entries_eval(n, kind, test_orient, src_orient, d, out, nullptr);
+}
+
+int voxcap_canonical_tensors(int D, double* ppar, double* epar, double* port, double* eort) {
+  VC_CHECK(D > 0 && (int64_t)D * D * D < ((int64_t)1 << 34), VOXCAP_ERR_ARG, "bad cube size");
+  return canonical_tensors(D, ppar, epar, port, eort);
 }
 
 int64_t voxcap_launch_count(void) { return vc::launch_count(); }

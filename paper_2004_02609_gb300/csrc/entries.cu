@@ -337,6 +337,36 @@ int build_toeplitz(Handle& h) {
   return VOXCAP_OK;
 }
 
+// ---- canonical tensors on an index cube (installation stage) ----
+__global__ void k_canonical(int D, double* ppar, double* epar, double* port, double* eort) {
+  const int64_t n = (int64_t)D * D * D;
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int e0 = (int)(t % D), e1 = (int)((t / D) % D), e2 = (int)(t / ((int64_t)D * D));
+  if (ppar || epar) {
+    double P, E;
+    par_pe((double)e0, (double)e1, (double)e2, &P, &E);
+    if (ppar) ppar[t] = P;
+    if (epar) epar[t] = E;
+  }
+  if (port || eort) {
+    double P, Ea, Eb;
+    ort_pe(e0 + 0.5, e1 + 0.5, (double)e2, &P, &Ea, &Eb);
+    if (port) port[t] = P;
+    if (eort) eort[t] = Ea;
+  }
+}
+
+int canonical_tensors(int D, double* ppar, double* epar, double* port, double* eort) {
+  VC_TRY(ensure_gl_tables());
+  const int64_t n = (int64_t)D * D * D;
+  const int TB = 128;
+  k_canonical<<<(unsigned)((n + TB - 1) / TB), TB>>>(D, ppar, epar, port, eort); ::vc::note_launch();
+  VC_CUDA(cudaGetLastError());
+  VC_CUDA(cudaDeviceSynchronize());
+  return VOXCAP_OK;
+}
+
 // ---- arbitrary panel pairs ----
 __global__ void k_entries(int n, const int32_t* __restrict__ kind, const int32_t* __restrict__ to,
                           const int32_t* __restrict__ so, const double* __restrict__ d,

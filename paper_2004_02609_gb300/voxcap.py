@@ -28,7 +28,12 @@ SYMBOLS = ["voxcap_default_opts", "voxcap_last_error", "voxcap_setup", "voxcap_d
            "voxcap_num_panels", "voxcap_panel_map", "voxcap_matvec", "voxcap_solve",
            "voxcap_capacitance", "voxcap_capacitance_grad", "voxcap_update_eps",
            "voxcap_entries", "voxcap_fft_length", "voxcap_toeplitz", "voxcap_launch_count",
-           "voxcap_matvec_noalloc"]
+           "voxcap_matvec_noalloc", "voxcap_tucker_expand", "voxcap_canonical_tensors"]
+
+
+class Tucker(ctypes.Structure):
+    _fields_ = [("dims", (ctypes.c_int * 3) * 4), ("ranks", (ctypes.c_int * 3) * 4),
+                ("core", ctypes.c_void_p * 4), ("factor", (ctypes.c_void_p * 3) * 4)]
 
 
 class Opts(ctypes.Structure):
@@ -36,7 +41,7 @@ class Opts(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("max_iters", ctypes.c_int),
                 ("max_sweeps", ctypes.c_int), ("nv", ctypes.c_int * 3),
                 ("precond", ctypes.c_int), ("pad_mode", ctypes.c_int),
-                ("use_tucker", ctypes.c_int)]
+                ("tucker", ctypes.POINTER(Tucker))]
 
 
 class Stats(ctypes.Structure):
@@ -85,6 +90,8 @@ def lib():
         L.voxcap_fft_length.argtypes = [vp, P(i32), P(i32), P(i32)]
         L.voxcap_toeplitz.argtypes = [vp, i32, vp, P(i32)]
         L.voxcap_matvec_noalloc.argtypes = [vp, vp, vp, i32, i32, i32]
+        L.voxcap_tucker_expand.argtypes = [vp, i32, i32, i32, vp, i32, vp, i32, vp, i32, vp]
+        L.voxcap_canonical_tensors.argtypes = [i32, vp, vp, vp, vp]
         L.voxcap_launch_count.argtypes = []
         L.voxcap_launch_count.restype = ctypes.c_int64
         _LIB = L
@@ -107,6 +114,11 @@ def default_opts(**kw) -> Opts:
             o.nv = (ctypes.c_int * 3)(*v)
         elif k == "precond" and isinstance(v, str):
             o.precond = PRECOND[v]
+        elif k == "tucker":
+            if v is not None:
+                t = v.as_ctypes()
+                o._tucker_ref = (v, t)
+                o.tucker = ctypes.pointer(t)
         elif k == "precision" and isinstance(v, str):
             o.precision = {"fp64": FP64, "fp32_refine": FP32_REFINE}[v]
         else:
@@ -290,6 +302,20 @@ class VoxCap:
             self.structs[s] = dict(n_cond=nc.value, n_diel=nd.value, n_conductors=m.value,
                                    offset=off.value)
         self.N = nt.value
+
+
+def tucker_expand(core, U1, U2, U3):
+    """X = core x1 U1 x2 U2 x3 U3 on the tensor cores (voxcap_tucker_expand);
+    torch CUDA float64 inputs, returns X[i, j, k] (numpy)."""
+    import torch
+    r1, r2, r3 = core.shape
+    D1, D2, D3 = U1.shape[0], U2.shape[0], U3.shape[0]
+    args = [t.contiguous().to(torch.float64) for t in (core, U1, U2, U3)]
+    out = torch.empty(D1 * D2 * D3, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    _check(lib().voxcap_tucker_expand(_ptr(args[0]), r1, r2, r3, _ptr(args[1]), D1, _ptr(args[2]), D2,
+                                      _ptr(args[3]), D3, _ptr(out)))
+    return out.cpu().numpy().reshape(D3, D2, D1).transpose(2, 1, 0)
 
 
 def launch_count() -> int:

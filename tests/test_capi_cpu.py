@@ -58,3 +58,21 @@ def test_errors_are_status_codes_without_gpu(libpath):
     h = ctypes.c_void_p()
     rc = L.voxcap_setup(None, 1, 1, 1, 1, None, None, 1, 1.0, None, None, ctypes.byref(h))
     assert rc == -1 and not h.value
+
+
+def test_struct_layouts_match_header(tmp_path, libpath):
+    """The ctypes mirrors of voxcap_opts / voxcap_stats / voxcap_tucker have
+    the sizes and field offsets the C compiler gives the header's structs."""
+    import ctypes
+    from paper_2004_02609_gb300 import voxcap as V
+    src = tmp_path / "sz.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "voxcap.h"\n'
+                   'int main(){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(voxcap_opts), '
+                   'sizeof(voxcap_stats), sizeof(voxcap_tucker), offsetof(voxcap_opts, tucker), '
+                   'offsetof(voxcap_opts, pad_mode), offsetof(voxcap_tucker, factor));return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    want = [ctypes.sizeof(V.Opts), ctypes.sizeof(V.Stats), ctypes.sizeof(V.Tucker),
+            V.Opts.tucker.offset, V.Opts.pad_mode.offset, V.Tucker.factor.offset]
+    assert got == want
