@@ -66,92 +66,141 @@ template <typename C> __device__ __forceinline__ C cmul_pi(C a) { return mk<C>(-
 // ---------------------------------------------------------------- FFT plans
 constexpr int kMaxStages = 24;
 
+// Exact x / d for x < 2^16 and 1 <= d < 2^16 by a multiply-high with
+// m = ceil(2^32 / d) (the error term x * (m d - 2^32) / 2^32 stays below 1/d).
+struct FastDiv {
+  uint32_t d, m;
+};
+__host__ __device__ __forceinline__ FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f;
+  f.d = d;
+  f.m = d <= 1 ? 0u : (uint32_t)((((uint64_t)1 << 32) + d - 1) / d);
+  return f;
+}
+__device__ __forceinline__ uint32_t fdiv(uint32_t x, const FastDiv& f) {
+  return f.d <= 1 ? x : __umulhi(x, f.m);
+}
+
 // A 1-D transform of length L factored into radices r[0..nst) in {2,3,4,5,7,8}.
-// tw points to L complex twiddles tw[m] = exp(-2 pi i m / L) in device memory.
+// Stage s combines sub-transforms of length Ns[s] with radix[s]; its twiddles
+// exp(-2 pi i r k / (Ns R)), k < Ns, 1 <= r < R, sit at stw[twoff[s] + k (R-1) + r - 1].
 template <typename C> struct Plan1D {
   int L;
   int nst;
   int radix[kMaxStages];
-  const C* tw;
+  int Ns[kMaxStages];
+  FastDiv fNs[kMaxStages];
+  int twoff[kMaxStages];
+  int twn;            // total number of stage twiddles
+  const C* stw;       // stage twiddles, device memory (copied to shared memory by the kernels)
 };
 
 bool factor_length(int L, int* radix, int* nst);   // host: false if not 2/3/5/7-smooth
 
-// ---------------------------------------------------------------- Stockham
-// Small DFTs: y[k] = sum_j v[j] w^(jk), w = exp(-+ 2 pi i / R).
-template <int R, typename C>
-__device__ __forceinline__ void dft(C* v, bool inv, const C* __restrict__ tw, int L) {
+// Copy the stage twiddles of a plan into shared memory (caller synchronises).
+template <typename C> __device__ __forceinline__ void load_twiddles(C* dst, const Plan1D<C>& p) {
+  for (int i = threadIdx.x; i < p.twn; i += blockDim.x) dst[i] = p.stw[i];
+}
+
+// ---------------------------------------------------------------- butterflies
+// y[k] = sum_j v[j] w^(jk), w = exp(-2 pi i / R) (forward) or its conjugate.
+template <typename C> __device__ __forceinline__ C cmul_i(C a, bool inv) {   // a * (-i) fwd, a * (+i) inv
+  return inv ? cmul_pi(a) : cmul_mi(a);
+}
+
+template <int R, typename C> __device__ __forceinline__ void dft(C* v, bool inv) {
+  using T = decltype(C::x);
   if constexpr (R == 2) {
     C a = v[0], b = v[1];
     v[0] = cadd(a, b); v[1] = csub(a, b);
+  } else if constexpr (R == 3) {
+    const T s = (T)0.8660254037844386467637;
+    C a = cadd(v[1], v[2]);
+    C t = csub(v[0], cscale(a, (T)0.5));
+    C u = cmul_i(cscale(csub(v[1], v[2]), s), inv);
+    v[0] = cadd(v[0], a);
+    v[1] = cadd(t, u);
+    v[2] = csub(t, u);
   } else if constexpr (R == 4) {
     C t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
-    C t2 = cadd(v[1], v[3]), t3 = csub(v[1], v[3]);
-    t3 = inv ? cmul_pi(t3) : cmul_mi(t3);
+    C t2 = cadd(v[1], v[3]), t3 = cmul_i(csub(v[1], v[3]), inv);
     v[0] = cadd(t0, t2); v[2] = csub(t0, t2);
     v[1] = cadd(t1, t3); v[3] = csub(t1, t3);
-  } else if constexpr (R == 8) {
-    // split into even / odd radix-4 halves
+  } else if constexpr (R == 5) {
+    const T c1 = (T)0.3090169943749474241023, c2 = (T)-0.8090169943749474241023;
+    const T s1 = (T)0.9510565162951535721164, s2 = (T)0.5877852522924731291687;
+    C a = cadd(v[1], v[4]), b = cadd(v[2], v[3]);
+    C d = csub(v[1], v[4]), e = csub(v[2], v[3]);
+    C t1 = cadd(v[0], cadd(cscale(a, c1), cscale(b, c2)));
+    C t2 = cadd(v[0], cadd(cscale(a, c2), cscale(b, c1)));
+    C u1 = cmul_i(cadd(cscale(d, s1), cscale(e, s2)), inv);
+    C u2 = cmul_i(csub(cscale(d, s2), cscale(e, s1)), inv);
+    v[0] = cadd(v[0], cadd(a, b));
+    v[1] = cadd(t1, u1); v[4] = csub(t1, u1);
+    v[2] = cadd(t2, u2); v[3] = csub(t2, u2);
+  } else if constexpr (R == 7) {
+    const T c1 = (T)0.623489801858733530525, c2 = (T)-0.2225209339563144042889,
+            c3 = (T)-0.9009688679024191262361;
+    const T s1 = (T)0.7818314824680298087084, s2 = (T)0.9749279121818236070181,
+            s3 = (T)0.4338837391175581204758;
+    C a1 = cadd(v[1], v[6]), a2 = cadd(v[2], v[5]), a3 = cadd(v[3], v[4]);
+    C d1 = csub(v[1], v[6]), d2 = csub(v[2], v[5]), d3 = csub(v[3], v[4]);
+    // cos(2 pi j k / 7) and sin(...) for k = 1, 2, 3 over the pairs j = 1, 2, 3
+    C t1 = cadd(v[0], cadd(cscale(a1, c1), cadd(cscale(a2, c2), cscale(a3, c3))));
+    C t2 = cadd(v[0], cadd(cscale(a1, c2), cadd(cscale(a2, c3), cscale(a3, c1))));
+    C t3 = cadd(v[0], cadd(cscale(a1, c3), cadd(cscale(a2, c1), cscale(a3, c2))));
+    C u1 = cmul_i(cadd(cscale(d1, s1), cadd(cscale(d2, s2), cscale(d3, s3))), inv);
+    C u2 = cmul_i(csub(cscale(d1, s2), cadd(cscale(d2, s3), cscale(d3, s1))), inv);
+    C u3 = cmul_i(cadd(cscale(d1, s3), csub(cscale(d3, s2), cscale(d2, s1))), inv);
+    v[0] = cadd(v[0], cadd(a1, cadd(a2, a3)));
+    v[1] = cadd(t1, u1); v[6] = csub(t1, u1);
+    v[2] = cadd(t2, u2); v[5] = csub(t2, u2);
+    v[3] = cadd(t3, u3); v[4] = csub(t3, u3);
+  } else {   // R == 8: two radix-4 halves
+    using TT = T;
     C e[4] = {v[0], v[2], v[4], v[6]};
     C o[4] = {v[1], v[3], v[5], v[7]};
-    dft<4, C>(e, inv, tw, L);
-    dft<4, C>(o, inv, tw, L);
-    using T = decltype(C::x);
-    const T h = (T)0.70710678118654752440084436210484903928;
-    // w8^k for k = 1,2,3 (forward: exp(-i pi k / 4))
+    dft<4, C>(e, inv);
+    dft<4, C>(o, inv);
+    const TT h = (TT)0.70710678118654752440084436210484903928;
     C w1 = inv ? mk<C>(h, h) : mk<C>(h, -h);
     C o1 = cmul(o[1], w1);
-    C o2 = inv ? cmul_pi(o[2]) : cmul_mi(o[2]);
+    C o2 = cmul_i(o[2], inv);
     C w3 = inv ? mk<C>(-h, h) : mk<C>(-h, -h);
     C o3 = cmul(o[3], w3);
     v[0] = cadd(e[0], o[0]); v[4] = csub(e[0], o[0]);
     v[1] = cadd(e[1], o1);   v[5] = csub(e[1], o1);
     v[2] = cadd(e[2], o2);   v[6] = csub(e[2], o2);
     v[3] = cadd(e[3], o3);   v[7] = csub(e[3], o3);
-  } else {
-    // odd prime radix: direct sum with the roots taken from the length-L table
-    C y[R];
-    const int step = L / R;
-#pragma unroll
-    for (int k = 0; k < R; ++k) {
-      C acc = v[0];
-#pragma unroll
-      for (int j = 1; j < R; ++j) {
-        C w = tw[((j * k) % R) * step];
-        if (inv) w.y = -w.y;
-        acc = cadd(acc, cmul(v[j], w));
-      }
-      y[k] = acc;
-    }
-#pragma unroll
-    for (int k = 0; k < R; ++k) v[k] = y[k];
   }
 }
 
-// One Stockham autosort stage (radix R, Ns = product of the radices done so
-// far) over `nlines` interleaved lines: element (pos, line) at pos*ld + line.
+// One Stockham autosort stage over `nlines` interleaved lines (element
+// (pos, line) at pos*ld + line); tw = this stage's twiddles in shared memory.
 template <int R, typename C>
-__device__ __forceinline__ void stockham_stage(const C* __restrict__ src, C* __restrict__ dst,
-                                               int L, int Ns, int nlines, int ld,
-                                               const C* __restrict__ tw, bool inv) {
+__device__ __forceinline__ void stockham_stage(const C* __restrict__ src, C* __restrict__ dst, int L,
+                                               int Ns, const FastDiv& fNs, int nlines,
+                                               const FastDiv& fnl, int ld, const C* __restrict__ tw,
+                                               bool inv) {
   const int nb = L / R;
-  const int twstride = L / (Ns * R);
-  for (int t = threadIdx.x; t < nb * nlines; t += blockDim.x) {
-    const int line = t % nlines;
-    const int j = t / nlines;
-    const int k = j % Ns;
+  const int total = nb * nlines;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int j = (int)fdiv((uint32_t)t, fnl);
+    const int line = t - j * nlines;
+    const int k = j - (int)fdiv((uint32_t)j, fNs) * Ns;
     C v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = src[(j + r * nb) * ld + line];
     if (Ns > 1) {
+      const C* w = tw + k * (R - 1);
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        C w = __ldg(&tw[r * k * twstride]);
-        if (inv) w.y = -w.y;
-        v[r] = cmul(v[r], w);
+        C ww = w[r - 1];
+        if (inv) ww.y = -ww.y;
+        v[r] = cmul(v[r], ww);
       }
     }
-    dft<R, C>(v, inv, tw, L);
+    dft<R, C>(v, inv);
     const int base = (j - k) * R + k;
 #pragma unroll
     for (int r = 0; r < R; ++r) dst[(base + r * Ns) * ld + line] = v[r];
@@ -159,25 +208,26 @@ __device__ __forceinline__ void stockham_stage(const C* __restrict__ src, C* __r
 }
 
 // Transform `nlines` lines held in shared memory (layout pos*ld + line);
-// `scr` is a scratch area of the same size.  Returns the buffer that holds
-// the result (buf or scr).  All threads of the block must call it.
+// `scr` is a scratch area of the same size and `stw` the plan's stage
+// twiddles in shared memory.  Returns the buffer holding the result.  All
+// threads of the block must call it.
 template <typename C>
-__device__ C* fft_lines(C* buf, C* scr, int nlines, int ld, const Plan1D<C>& p, bool inv) {
+__device__ C* fft_lines(C* buf, C* scr, int nlines, int ld, const Plan1D<C>& p, const C* stw, bool inv) {
   C* src = buf;
   C* dst = scr;
-  int Ns = 1;
+  const FastDiv fnl = make_fastdiv((uint32_t)nlines);
   for (int s = 0; s < p.nst; ++s) {
     const int R = p.radix[s];
+    const C* tw = stw + p.twoff[s];
     switch (R) {
-      case 2: stockham_stage<2, C>(src, dst, p.L, Ns, nlines, ld, p.tw, inv); break;
-      case 3: stockham_stage<3, C>(src, dst, p.L, Ns, nlines, ld, p.tw, inv); break;
-      case 4: stockham_stage<4, C>(src, dst, p.L, Ns, nlines, ld, p.tw, inv); break;
-      case 5: stockham_stage<5, C>(src, dst, p.L, Ns, nlines, ld, p.tw, inv); break;
-      case 7: stockham_stage<7, C>(src, dst, p.L, Ns, nlines, ld, p.tw, inv); break;
-      default: stockham_stage<8, C>(src, dst, p.L, Ns, nlines, ld, p.tw, inv); break;
+      case 2: stockham_stage<2, C>(src, dst, p.L, p.Ns[s], p.fNs[s], nlines, fnl, ld, tw, inv); break;
+      case 3: stockham_stage<3, C>(src, dst, p.L, p.Ns[s], p.fNs[s], nlines, fnl, ld, tw, inv); break;
+      case 4: stockham_stage<4, C>(src, dst, p.L, p.Ns[s], p.fNs[s], nlines, fnl, ld, tw, inv); break;
+      case 5: stockham_stage<5, C>(src, dst, p.L, p.Ns[s], p.fNs[s], nlines, fnl, ld, tw, inv); break;
+      case 7: stockham_stage<7, C>(src, dst, p.L, p.Ns[s], p.fNs[s], nlines, fnl, ld, tw, inv); break;
+      default: stockham_stage<8, C>(src, dst, p.L, p.Ns[s], p.fNs[s], nlines, fnl, ld, tw, inv); break;
     }
     __syncthreads();
-    Ns *= R;
     C* t = src; src = dst; dst = t;
   }
   return src;

@@ -90,6 +90,8 @@ __global__ void k_xfwd(MvmArgs a, const T* __restrict__ xin, C_t<T>* __restrict_
   const int M = g.Mx, H = g.Hx;
   C* buf = reinterpret_cast<C*>(smem_raw);
   C* scr = buf + (size_t)M * NL;
+  C* stw = scr + (size_t)M * NL;
+  load_twiddles(stw, plan);
   const int z = blockIdx.y;
   const int bg = blockIdx.z;             // b * 3 + grid
   const int grid = bg % 3, b = bg / 3;
@@ -121,7 +123,7 @@ __global__ void k_xfwd(MvmArgs a, const T* __restrict__ xin, C_t<T>* __restrict_
     buf[x * NL + l] = mk<C>(re, im);
   }
   __syncthreads();
-  C* res = fft_lines(buf, scr, NL, NL, plan, false);
+  C* res = fft_lines(buf, scr, NL, NL, plan, stw, false);
   const int GI = ADJ ? 6 : 3;
   for (int t = threadIdx.x; t < H * NL; t += blockDim.x) {
     const int l = t % NL, k = t / NL;
@@ -159,6 +161,8 @@ __global__ void k_ypass(Geom g, int G, const C_t<T>* __restrict__ in, C_t<T>* __
   const int M = g.My, H = g.Hx;
   C* buf = reinterpret_cast<C*>(smem_raw);
   C* scr = buf + (size_t)M * TX;
+  C* stw = scr + (size_t)M * TX;
+  load_twiddles(stw, plan);
   const int k0 = blockIdx.x * TX;
   const int z = blockIdx.y;
   const int bg = blockIdx.z;           // b * G + grid
@@ -179,7 +183,7 @@ __global__ void k_ypass(Geom g, int G, const C_t<T>* __restrict__ in, C_t<T>* __
     buf[y * TX + c] = v;
   }
   __syncthreads();
-  C* res = fft_lines(buf, scr, TX, TX, plan, INV);
+  C* res = fft_lines(buf, scr, TX, TX, plan, stw, INV);
   for (int t = threadIdx.x; t < Lout * TX; t += blockDim.x) {
     const int c = t % TX, y = t / TX;
     const int kx = k0 + c;
@@ -204,6 +208,8 @@ __global__ void k_zmac(Geom g, C_t<T>* __restrict__ data, const T* __restrict__ 
   const int M = g.Mz, H = g.Hx;
   C* bufA = reinterpret_cast<C*>(smem_raw);
   C* bufB = bufA + (size_t)M * 6 * TX;
+  C* stw = bufB + (size_t)M * 6 * TX;
+  load_twiddles(stw, plan);
   const int b = blockIdx.x;
   const int k0 = blockIdx.y * TX;
   const int ky = blockIdx.z;
@@ -219,7 +225,7 @@ __global__ void k_zmac(Geom g, C_t<T>* __restrict__ data, const T* __restrict__ 
     bufA[z * LI + col] = v;
   }
   __syncthreads();
-  C* res = fft_lines(bufA, bufB, LI, LI, plan, false);
+  C* res = fft_lines(bufA, bufB, LI, LI, plan, stw, false);
   C* outb = (res == bufA) ? bufB : bufA;
   const int LO = GO * TX;
   const int64_t Otot = (int64_t)H * g.Oy * g.Oz;
@@ -282,7 +288,7 @@ __global__ void k_zmac(Geom g, C_t<T>* __restrict__ data, const T* __restrict__ 
     for (int q = 0; q < GO; ++q) outb[kz * LO + q * TX + c] = o[q];
   }
   __syncthreads();
-  C* res2 = fft_lines(outb, res, LO, LO, plan, true);
+  C* res2 = fft_lines(outb, res, LO, LO, plan, stw, true);
   for (int t = threadIdx.x; t < g.Lz * LO; t += blockDim.x) {
     const int col = t % LO, z = t / LO;
     const int grid = col / TX, c = col % TX;
@@ -305,6 +311,8 @@ __global__ void k_xinv(MvmArgs a, const C_t<T>* __restrict__ in, const T* __rest
   constexpr int GO = ADJ ? 3 : 6;
   C* buf = reinterpret_cast<C*>(smem_raw);
   C* scr = buf + (size_t)M * NL;
+  C* stw = scr + (size_t)M * NL;
+  load_twiddles(stw, plan);
   const int z = blockIdx.y;
   const int bo = blockIdx.z;            // b * 3 + orientation
   const int al = bo % 3, b = bo / 3;
@@ -344,7 +352,7 @@ __global__ void k_xinv(MvmArgs a, const C_t<T>* __restrict__ in, const T* __rest
     buf[k * NL + l] = v;
   }
   __syncthreads();
-  C* res = fft_lines(buf, scr, NL, NL, plan, true);
+  C* res = fft_lines(buf, scr, NL, NL, plan, stw, true);
   const int32_t* fm = a.fmap + (((int64_t)s * 3 + al) * g.Lz + z) * ((int64_t)g.Ly * g.Lx);
   const T* xr = xin + (int64_t)r * a.N;
   T* yr = yout + (int64_t)r * a.N;
@@ -433,7 +441,7 @@ int mvm(Handle& h, const T* x, T* y, int nrhs, bool adjoint, T* field_out, void*
     const int NL = smem_lines<T>(g.Mx, 1, 16);
     const int lines = adjoint ? g.Ly : (g.Ly + 1) / 2;
     dim3 grid((lines + NL - 1) / NL, g.Lz, B * 3);
-    size_t sm = 2 * (size_t)g.Mx * NL * sizeof(C);
+    size_t sm = (2 * (size_t)g.Mx * NL + plan_of<T>(h, 0).twn) * sizeof(C);
     if (adjoint) {
       VC_TRY(set_smem<T>(k_xfwd<T, true>, sm));
       k_xfwd<T, true><<<grid, TB, sm, st>>>(a, x, bufX, plan_of<T>(h, 0), phase_of<T>(h, 0), NL); ::vc::note_launch();
@@ -447,7 +455,7 @@ int mvm(Handle& h, const T* x, T* y, int nrhs, bool adjoint, T* field_out, void*
   // stride differs (6 grids allocated), so launch per batch item block.
   const int TXy = smem_lines<T>(g.My, 1, 16);
   {
-    size_t sm = 2 * (size_t)g.My * TXy * sizeof(C);
+    size_t sm = (2 * (size_t)g.My * TXy + plan_of<T>(h, 1).twn) * sizeof(C);
     VC_TRY(set_smem<T>(k_ypass<T, false>, sm));
     dim3 grid((g.Hx + TXy - 1) / TXy, g.Lz, B * GI);
     k_ypass<T, false><<<grid, TB, sm, st>>>(g, GI, bufX, bufY, (int64_t)GI * gX, (int64_t)6 * gY,
@@ -457,7 +465,7 @@ int mvm(Handle& h, const T* x, T* y, int nrhs, bool adjoint, T* field_out, void*
   // zmac
   {
     const int TXz = smem_lines<T>(g.Mz, 6, 16);
-    size_t sm = 2 * (size_t)g.Mz * 6 * TXz * sizeof(C);
+    size_t sm = (2 * (size_t)g.Mz * 6 * TXz + plan_of<T>(h, 2).twn) * sizeof(C);
     dim3 grid(B, (g.Hx + TXz - 1) / TXz, g.My);
     if (adjoint) {
       VC_TRY(set_smem<T>(k_zmac<T, true>, sm));
@@ -472,7 +480,7 @@ int mvm(Handle& h, const T* x, T* y, int nrhs, bool adjoint, T* field_out, void*
   }
   // yinv: bufY [B][6] (first GO grids) -> bufX [B][GO]
   {
-    size_t sm = 2 * (size_t)g.My * TXy * sizeof(C);
+    size_t sm = (2 * (size_t)g.My * TXy + plan_of<T>(h, 1).twn) * sizeof(C);
     VC_TRY(set_smem<T>(k_ypass<T, true>, sm));
     dim3 grid((g.Hx + TXy - 1) / TXy, g.Lz, B * GO);
     k_ypass<T, true><<<grid, TB, sm, st>>>(g, GO, bufY, bufX, (int64_t)6 * gY, (int64_t)GO * gX,
@@ -484,7 +492,7 @@ int mvm(Handle& h, const T* x, T* y, int nrhs, bool adjoint, T* field_out, void*
     const int NL = smem_lines<T>(g.Mx, 1, 16);
     const int lines = adjoint ? (g.Ly + 1) / 2 : g.Ly;
     dim3 grid((lines + NL - 1) / NL, g.Lz, B * 3);
-    size_t sm = 2 * (size_t)g.Mx * NL * sizeof(C);
+    size_t sm = (2 * (size_t)g.Mx * NL + plan_of<T>(h, 0).twn) * sizeof(C);
     if (adjoint) {
       VC_TRY(set_smem<T>(k_xinv<T, true>, sm));
       k_xinv<T, true><<<grid, TB, sm, st>>>(a, bufX, x, y, field_out, plan_of<T>(h, 0),

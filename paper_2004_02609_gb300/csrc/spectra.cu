@@ -35,15 +35,30 @@ static int pick_length(int N, int mode) {
   return m;
 }
 
+// Stage twiddles of a radix plan (see Plan1D) and the half-voxel phases
+// exp(+i pi m / L), computed in long double and rounded once.
 template <typename C>
-static void fill_twiddles(std::vector<C>& tw, std::vector<C>& ph, int L) {
-  tw.resize(L);
-  ph.resize(L);
+static void fill_tables(std::vector<C>& stw, std::vector<C>& ph, int L, const int* radix, int nst,
+                        int* Ns, int* twoff) {
   const long double pi = 3.141592653589793238462643383279502884L;
+  stw.clear();
+  int ns = 1;
+  for (int s = 0; s < nst; ++s) {
+    const int R = radix[s];
+    Ns[s] = ns;
+    twoff[s] = (int)stw.size();
+    for (int k = 0; k < ns; ++k)
+      for (int r = 1; r < R; ++r) {
+        long double a = -2.0L * pi * (long double)(r * k) / (long double)(ns * R);
+        C c;
+        c.x = (decltype(C::x))std::cos(a);
+        c.y = (decltype(C::x))std::sin(a);
+        stw.push_back(c);
+      }
+    ns *= R;
+  }
+  ph.resize(L);
   for (int m = 0; m < L; ++m) {
-    long double a = -2.0L * pi * (long double)m / (long double)L;
-    tw[m].x = (decltype(C::x))std::cos(a);
-    tw[m].y = (decltype(C::x))std::sin(a);
     long double b = pi * (long double)m / (long double)L;
     ph[m].x = (decltype(C::x))std::cos(b);
     ph[m].y = (decltype(C::x))std::sin(b);
@@ -56,24 +71,32 @@ int build_fft_plans(Handle& h) {
   int M[3];
   for (int a = 0; a < 3; ++a) {
     M[a] = pick_length(n[a], h.opts.pad_mode);
-    int rad[kMaxStages], nst = 0;
+    int rad[kMaxStages], nst = 0, Ns[kMaxStages], twoff[kMaxStages];
     VC_CHECK(factor_length(M[a], rad, &nst), VOXCAP_ERR_UNSUPPORTED,
              "FFT length " + std::to_string(M[a]) + " is not 2/3/5/7-smooth (use pad_mode 0)");
     std::vector<double2> twd, phd;
     std::vector<float2> twf, phf;
-    fill_twiddles(twd, phd, M[a]);
-    fill_twiddles(twf, phf, M[a]);
-    VC_TRY(h.twd[a].alloc(M[a])); VC_TRY(h.twf[a].alloc(M[a]));
+    fill_tables(twd, phd, M[a], rad, nst, Ns, twoff);
+    fill_tables(twf, phf, M[a], rad, nst, Ns, twoff);
+    const size_t ntw = std::max<size_t>(twd.size(), 1);
+    VC_TRY(h.twd[a].alloc(ntw)); VC_TRY(h.twf[a].alloc(ntw));
     VC_TRY(h.phd[a].alloc(M[a])); VC_TRY(h.phf[a].alloc(M[a]));
-    VC_CUDA(cudaMemcpy(h.twd[a].p, twd.data(), sizeof(double2) * M[a], cudaMemcpyHostToDevice));
-    VC_CUDA(cudaMemcpy(h.twf[a].p, twf.data(), sizeof(float2) * M[a], cudaMemcpyHostToDevice));
+    if (!twd.empty()) {
+      VC_CUDA(cudaMemcpy(h.twd[a].p, twd.data(), sizeof(double2) * twd.size(), cudaMemcpyHostToDevice));
+      VC_CUDA(cudaMemcpy(h.twf[a].p, twf.data(), sizeof(float2) * twf.size(), cudaMemcpyHostToDevice));
+    }
     VC_CUDA(cudaMemcpy(h.phd[a].p, phd.data(), sizeof(double2) * M[a], cudaMemcpyHostToDevice));
     VC_CUDA(cudaMemcpy(h.phf[a].p, phf.data(), sizeof(float2) * M[a], cudaMemcpyHostToDevice));
-    h.pd[a].L = h.pf[a].L = M[a];
-    h.pd[a].nst = h.pf[a].nst = nst;
-    for (int s = 0; s < nst; ++s) h.pd[a].radix[s] = h.pf[a].radix[s] = rad[s];
-    h.pd[a].tw = h.twd[a].p;
-    h.pf[a].tw = h.twf[a].p;
+    for (Plan1D<double2>* pd : {&h.pd[a]}) {
+      pd->L = M[a]; pd->nst = nst; pd->twn = (int)twd.size(); pd->stw = h.twd[a].p;
+    }
+    h.pf[a].L = M[a]; h.pf[a].nst = nst; h.pf[a].twn = (int)twf.size(); h.pf[a].stw = h.twf[a].p;
+    for (int s = 0; s < nst; ++s) {
+      h.pd[a].radix[s] = h.pf[a].radix[s] = rad[s];
+      h.pd[a].Ns[s] = h.pf[a].Ns[s] = Ns[s];
+      h.pd[a].fNs[s] = h.pf[a].fNs[s] = make_fastdiv((uint32_t)Ns[s]);
+      h.pd[a].twoff[s] = h.pf[a].twoff[s] = twoff[s];
+    }
   }
   g.Mx = M[0]; g.My = M[1]; g.Mz = M[2];
   g.Hx = g.Mx / 2 + 1;
@@ -145,6 +168,8 @@ __global__ void k_rows_r2c(const T* __restrict__ in, int64_t nrows, int M, int H
   extern __shared__ unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   C* scr = buf + (size_t)M * NL;
+  C* stw = scr + (size_t)M * NL;
+  load_twiddles(stw, plan);
   const int64_t row0 = (int64_t)blockIdx.x * NL * 2;
   for (int t = threadIdx.x; t < M * NL; t += blockDim.x) {
     int l = t % NL, x = t / NL;
@@ -154,7 +179,7 @@ __global__ void k_rows_r2c(const T* __restrict__ in, int64_t nrows, int M, int H
     buf[x * NL + l] = mk<C>(a, b);
   }
   __syncthreads();
-  C* res = fft_lines(buf, scr, NL, NL, plan, false);
+  C* res = fft_lines(buf, scr, NL, NL, plan, stw, false);
   for (int t = threadIdx.x; t < H * NL; t += blockDim.x) {
     int l = t % NL, k = t / NL;
     int64_t ra = row0 + 2 * l, rb = ra + 1;
@@ -176,6 +201,8 @@ __global__ void k_strided_c2c(C_t<T>* __restrict__ data, int64_t outer, int L, i
   extern __shared__ unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   C* scr = buf + (size_t)L * TX;
+  C* stw = scr + (size_t)L * TX;
+  load_twiddles(stw, plan);
   const int64_t tiles = (inner + TX - 1) / TX;
   const int64_t o = blockIdx.x / tiles;
   const int64_t i0 = (blockIdx.x % tiles) * TX;
@@ -186,7 +213,7 @@ __global__ void k_strided_c2c(C_t<T>* __restrict__ data, int64_t outer, int L, i
     buf[p * TX + c] = ii < inner ? base[(int64_t)p * inner + ii] : mk<C>((T)0, (T)0);
   }
   __syncthreads();
-  C* res = fft_lines(buf, scr, TX, TX, plan, inv);
+  C* res = fft_lines(buf, scr, TX, TX, plan, stw, inv);
   for (int t = threadIdx.x; t < L * TX; t += blockDim.x) {
     int c = t % TX, p = t / TX;
     int64_t ii = i0 + c;
@@ -252,7 +279,7 @@ int build_spectra(Handle& h) {
       int NL = smem_limit_lines<double>(g.Mx, 16);
       int64_t nrows = (int64_t)g.My * g.Mz;
       unsigned nblk = (unsigned)((nrows + 2 * NL - 1) / (2 * NL));
-      size_t sm = 2 * (size_t)g.Mx * NL * sizeof(double2);
+      size_t sm = (2 * (size_t)g.Mx * NL + h.pd[0].twn) * sizeof(double2);
       VC_CUDA(cudaFuncSetAttribute(k_rows_r2c<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
       k_rows_r2c<double><<<nblk, 256, sm, h.stream>>>(circ.p, nrows, g.Mx, g.Hx, spec.p, h.pd[0], NL); ::vc::note_launch();
       VC_CUDA(cudaGetLastError());
@@ -261,7 +288,7 @@ int build_spectra(Handle& h) {
     {
       int TX = smem_limit_lines<double>(g.My, 16);
       int64_t tiles = (g.Hx + TX - 1) / TX;
-      size_t sm = 2 * (size_t)g.My * TX * sizeof(double2);
+      size_t sm = (2 * (size_t)g.My * TX + h.pd[1].twn) * sizeof(double2);
       VC_CUDA(cudaFuncSetAttribute(k_strided_c2c<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
       k_strided_c2c<double><<<(unsigned)(g.Mz * tiles), 256, sm, h.stream>>>(
           spec.p, g.Mz, g.My, g.Hx, h.pd[1], TX, false); ::vc::note_launch();
@@ -272,7 +299,7 @@ int build_spectra(Handle& h) {
       int TX = smem_limit_lines<double>(g.Mz, 16);
       int64_t inner = (int64_t)g.My * g.Hx;
       int64_t tiles = (inner + TX - 1) / TX;
-      size_t sm = 2 * (size_t)g.Mz * TX * sizeof(double2);
+      size_t sm = (2 * (size_t)g.Mz * TX + h.pd[2].twn) * sizeof(double2);
       VC_CUDA(cudaFuncSetAttribute(k_strided_c2c<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
       k_strided_c2c<double><<<(unsigned)tiles, 256, sm, h.stream>>>(spec.p, 1, g.Mz, inner, h.pd[2],
                                                                    TX, false); ::vc::note_launch();

@@ -153,6 +153,28 @@ def test_matvec_matches_dense(w, pad_mode):
         assert rel_l2(y32[r], ref[r]) < 2e-6
 
 
+@pytest.mark.parametrize("shape", [(6, 4, 5), (12, 3, 17), (24, 10, 6)])
+def test_matvec_every_radix(shape):
+    """Grids whose padded lengths need every radix of the FFT engine
+    (14, 10, 12 / 28, 8, 36 / 50, 24, 14 = 2,3,4,5,7,8 factors): forward and
+    transposed products against the dense oracle, FP64 and FP32."""
+    import torch
+    w = W.random_structure(shape, 9, n_cond=2)
+    vc = make(w)
+    radices = {p for M in vc.fft_lengths() for p in (2, 3, 5, 7) if M % p == 0}
+    ps, A = dense(w)
+    X = np.random.default_rng(3).standard_normal((2, ps.n))
+    x64 = torch.tensor(X, device="cuda")
+    y = vc.matvec(x64).cpu().numpy()
+    yT = vc.matvec(x64, adjoint=True).cpu().numpy()
+    y32 = vc.matvec(x64.float()).cpu().numpy()
+    for r in range(2):
+        assert rel_l2(y[r], A @ X[r]) < 1e-12
+        assert rel_l2(yT[r], A.T @ X[r]) < 1e-12
+        assert rel_l2(y32[r], A @ X[r]) < 2e-6
+    assert radices
+
+
 def test_matvec_paper_padding_equals_smooth_padding():
     """Any padded length >= 2N+1 gives the same linear convolution (Appendix B):
     the paper's 2(N+1) and the smooth length agree to rounding."""
