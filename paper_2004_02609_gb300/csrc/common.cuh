@@ -175,18 +175,17 @@ template <int R, typename C> __device__ __forceinline__ void dft(C* v, bool inv)
   }
 }
 
-// One Stockham autosort stage over `nlines` interleaved lines (element
-// (pos, line) at pos*ld + line); tw = this stage's twiddles in shared memory.
-template <int R, typename C>
+// One Stockham autosort stage over NL interleaved lines (element (pos, line)
+// at pos*ld + line); tw = this stage's twiddles in shared memory.
+template <int R, int NL, typename C>
 __device__ __forceinline__ void stockham_stage(const C* __restrict__ src, C* __restrict__ dst, int L,
-                                               int Ns, const FastDiv& fNs, int nlines,
-                                               const FastDiv& fnl, int ld, const C* __restrict__ tw,
-                                               bool inv) {
+                                               int Ns, const FastDiv& fNs, int ld,
+                                               const C* __restrict__ tw, bool inv) {
   const int nb = L / R;
-  const int total = nb * nlines;
+  const int total = nb * NL;
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
-    const int j = (int)fdiv((uint32_t)t, fnl);
-    const int line = t - j * nlines;
+    const int j = t / NL;
+    const int line = t - j * NL;
     const int k = j - (int)fdiv((uint32_t)j, fNs) * Ns;
     C v[R];
 #pragma unroll
@@ -207,31 +206,40 @@ __device__ __forceinline__ void stockham_stage(const C* __restrict__ src, C* __r
   }
 }
 
-// Transform `nlines` lines held in shared memory (layout pos*ld + line);
-// `scr` is a scratch area of the same size and `stw` the plan's stage
-// twiddles in shared memory.  Returns the buffer holding the result.  All
-// threads of the block must call it.
-template <typename C>
-__device__ C* fft_lines(C* buf, C* scr, int nlines, int ld, const Plan1D<C>& p, const C* stw, bool inv) {
+// Transform NL lines held in shared memory (layout pos*ld + line); `scr` is a
+// scratch area of the same size and `stw` the plan's stage twiddles in shared
+// memory.  Returns the buffer holding the result.  All threads of the block
+// must call it.
+template <int NL, typename C>
+__device__ C* fft_lines(C* buf, C* scr, int ld, const Plan1D<C>& p, const C* stw, bool inv) {
   C* src = buf;
   C* dst = scr;
-  const FastDiv fnl = make_fastdiv((uint32_t)nlines);
   for (int s = 0; s < p.nst; ++s) {
     const int R = p.radix[s];
     const C* tw = stw + p.twoff[s];
     switch (R) {
-      case 2: stockham_stage<2, C>(src, dst, p.L, p.Ns[s], p.fNs[s], nlines, fnl, ld, tw, inv); break;
-      case 3: stockham_stage<3, C>(src, dst, p.L, p.Ns[s], p.fNs[s], nlines, fnl, ld, tw, inv); break;
-      case 4: stockham_stage<4, C>(src, dst, p.L, p.Ns[s], p.fNs[s], nlines, fnl, ld, tw, inv); break;
-      case 5: stockham_stage<5, C>(src, dst, p.L, p.Ns[s], p.fNs[s], nlines, fnl, ld, tw, inv); break;
-      case 7: stockham_stage<7, C>(src, dst, p.L, p.Ns[s], p.fNs[s], nlines, fnl, ld, tw, inv); break;
-      default: stockham_stage<8, C>(src, dst, p.L, p.Ns[s], p.fNs[s], nlines, fnl, ld, tw, inv); break;
+      case 2: stockham_stage<2, NL, C>(src, dst, p.L, p.Ns[s], p.fNs[s], ld, tw, inv); break;
+      case 3: stockham_stage<3, NL, C>(src, dst, p.L, p.Ns[s], p.fNs[s], ld, tw, inv); break;
+      case 4: stockham_stage<4, NL, C>(src, dst, p.L, p.Ns[s], p.fNs[s], ld, tw, inv); break;
+      case 5: stockham_stage<5, NL, C>(src, dst, p.L, p.Ns[s], p.fNs[s], ld, tw, inv); break;
+      case 7: stockham_stage<7, NL, C>(src, dst, p.L, p.Ns[s], p.fNs[s], ld, tw, inv); break;
+      default: stockham_stage<8, NL, C>(src, dst, p.L, p.Ns[s], p.fNs[s], ld, tw, inv); break;
     }
     __syncthreads();
     C* t = src; src = dst; dst = t;
   }
   return src;
 }
+
+// Dispatch a power-of-two tile width (1..16) to a template instantiation.
+#define VC_TILE_DISPATCH(W, F) \
+  switch (W) {                 \
+    case 1: F(1); break;       \
+    case 2: F(2); break;       \
+    case 4: F(4); break;       \
+    case 8: F(8); break;       \
+    default: F(16); break;     \
+  }
 
 // ---------------------------------------------------------------- scan
 // exclusive prefix sum of n int32 values in place on the device; tmp must hold

@@ -81,9 +81,9 @@ template <> __device__ __forceinline__ double idiag_of<double>(const MvmArgs& a,
 // ------------------------------------------------------------------ xfwd
 // Forward: line l = rows (2l, 2l+1) of grid g.  Adjoint: line l = row l of
 // the conductor-source grid g (real part) and dielectric-source grid g (imag).
-template <typename T, bool ADJ>
+template <typename T, bool ADJ, int NL>
 __global__ void k_xfwd(MvmArgs a, const T* __restrict__ xin, C_t<T>* __restrict__ out,
-                       Plan1D<C_t<T>> plan, const C_t<T>* __restrict__ phx, int NL) {
+                       Plan1D<C_t<T>> plan, const C_t<T>* __restrict__ phx) {
   using C = C_t<T>;
   extern __shared__ unsigned char smem_raw[];
   const Geom& g = a.g;
@@ -123,7 +123,7 @@ __global__ void k_xfwd(MvmArgs a, const T* __restrict__ xin, C_t<T>* __restrict_
     buf[x * NL + l] = mk<C>(re, im);
   }
   __syncthreads();
-  C* res = fft_lines(buf, scr, NL, NL, plan, stw, false);
+  C* res = fft_lines<NL>(buf, scr, NL, plan, stw, false);
   const int GI = ADJ ? 6 : 3;
   for (int t = threadIdx.x; t < H * NL; t += blockDim.x) {
     const int l = t % NL, k = t / NL;
@@ -152,10 +152,10 @@ __global__ void k_xfwd(MvmArgs a, const T* __restrict__ xin, C_t<T>* __restrict_
 // in: [B][G][Lz][Lin][H] -> out: [B][G][Lz][Lout][H], transform along the
 // second-fastest axis.  Forward: Lin = Ly (zero-padded to My), Lout = My,
 // phase after.  Inverse: Lin = My, Lout = Ly (truncated), conj phase before.
-template <typename T, bool INV>
+template <typename T, bool INV, int TX>
 __global__ void k_ypass(Geom g, int G, const C_t<T>* __restrict__ in, C_t<T>* __restrict__ out,
                         int64_t in_bstride, int64_t out_bstride,
-                        Plan1D<C_t<T>> plan, const C_t<T>* __restrict__ phy, int TX) {
+                        Plan1D<C_t<T>> plan, const C_t<T>* __restrict__ phy) {
   using C = C_t<T>;
   extern __shared__ unsigned char smem_raw[];
   const int M = g.My, H = g.Hx;
@@ -183,7 +183,7 @@ __global__ void k_ypass(Geom g, int G, const C_t<T>* __restrict__ in, C_t<T>* __
     buf[y * TX + c] = v;
   }
   __syncthreads();
-  C* res = fft_lines(buf, scr, TX, TX, plan, stw, INV);
+  C* res = fft_lines<TX>(buf, scr, TX, plan, stw, INV);
   for (int t = threadIdx.x; t < Lout * TX; t += blockDim.x) {
     const int c = t % TX, y = t / TX;
     const int kx = k0 + c;
@@ -198,9 +198,9 @@ __global__ void k_ypass(Geom g, int G, const C_t<T>* __restrict__ in, C_t<T>* __
 // data: [B][6][Lz][My][H] (in place).  Forward reads grids 0..2, writes 0..5
 // (potential x,y,z then field x,y,z).  Adjoint reads 0..5 (conductor-source
 // x,y,z then dielectric-source x,y,z) and writes 0..2.
-template <typename T, bool ADJ>
+template <typename T, bool ADJ, int TX>
 __global__ void k_zmac(Geom g, C_t<T>* __restrict__ data, const T* __restrict__ spec,
-                       Plan1D<C_t<T>> plan, const C_t<T>* __restrict__ phz, int TX) {
+                       Plan1D<C_t<T>> plan, const C_t<T>* __restrict__ phz) {
   using C = C_t<T>;
   extern __shared__ unsigned char smem_raw[];
   constexpr int GI = ADJ ? 6 : 3;
@@ -215,7 +215,7 @@ __global__ void k_zmac(Geom g, C_t<T>* __restrict__ data, const T* __restrict__ 
   const int ky = blockIdx.z;
   const int64_t gstride = (int64_t)g.Lz * g.My * H;     // one grid of one batch item
   C* base = data + (int64_t)b * 6 * gstride + (int64_t)ky * H;
-  const int LI = GI * TX;
+  constexpr int LI = GI * TX;
   for (int t = threadIdx.x; t < M * LI; t += blockDim.x) {
     const int col = t % LI, z = t / LI;
     const int grid = col / TX, c = col % TX;
@@ -225,9 +225,9 @@ __global__ void k_zmac(Geom g, C_t<T>* __restrict__ data, const T* __restrict__ 
     bufA[z * LI + col] = v;
   }
   __syncthreads();
-  C* res = fft_lines(bufA, bufB, LI, LI, plan, stw, false);
+  C* res = fft_lines<LI>(bufA, bufB, LI, plan, stw, false);
   C* outb = (res == bufA) ? bufB : bufA;
-  const int LO = GO * TX;
+  constexpr int LO = GO * TX;
   const int64_t Otot = (int64_t)H * g.Oy * g.Oz;
   const bool fy = ky > g.My / 2;
   const int kyf = fy ? g.My - ky : ky;
@@ -288,7 +288,7 @@ __global__ void k_zmac(Geom g, C_t<T>* __restrict__ data, const T* __restrict__ 
     for (int q = 0; q < GO; ++q) outb[kz * LO + q * TX + c] = o[q];
   }
   __syncthreads();
-  C* res2 = fft_lines(outb, res, LO, LO, plan, stw, true);
+  C* res2 = fft_lines<LO>(outb, res, LO, plan, stw, true);
   for (int t = threadIdx.x; t < g.Lz * LO; t += blockDim.x) {
     const int col = t % LO, z = t / LO;
     const int grid = col / TX, c = col % TX;
@@ -300,10 +300,10 @@ __global__ void k_zmac(Geom g, C_t<T>* __restrict__ data, const T* __restrict__ 
 // ------------------------------------------------------------------ xinv
 // Forward: line = row y of output orientation a: potential row (grid a) and
 // field row (grid 3+a) -> gather.  Adjoint: line = rows (2l, 2l+1) of grid a.
-template <typename T, bool ADJ>
+template <typename T, bool ADJ, int NL>
 __global__ void k_xinv(MvmArgs a, const C_t<T>* __restrict__ in, const T* __restrict__ xin,
                        T* __restrict__ yout, T* __restrict__ field, Plan1D<C_t<T>> plan,
-                       const C_t<T>* __restrict__ phx, int NL) {
+                       const C_t<T>* __restrict__ phx) {
   using C = C_t<T>;
   extern __shared__ unsigned char smem_raw[];
   const Geom& g = a.g;
@@ -352,7 +352,7 @@ __global__ void k_xinv(MvmArgs a, const C_t<T>* __restrict__ in, const T* __rest
     buf[k * NL + l] = v;
   }
   __syncthreads();
-  C* res = fft_lines(buf, scr, NL, NL, plan, stw, true);
+  C* res = fft_lines<NL>(buf, scr, NL, plan, stw, true);
   const int32_t* fm = a.fmap + (((int64_t)s * 3 + al) * g.Lz + z) * ((int64_t)g.Ly * g.Lx);
   const T* xr = xin + (int64_t)r * a.N;
   T* yr = yout + (int64_t)r * a.N;
@@ -442,24 +442,31 @@ int mvm(Handle& h, const T* x, T* y, int nrhs, bool adjoint, T* field_out, void*
     const int lines = adjoint ? g.Ly : (g.Ly + 1) / 2;
     dim3 grid((lines + NL - 1) / NL, g.Lz, B * 3);
     size_t sm = (2 * (size_t)g.Mx * NL + plan_of<T>(h, 0).twn) * sizeof(C);
-    if (adjoint) {
-      VC_TRY(set_smem<T>(k_xfwd<T, true>, sm));
-      k_xfwd<T, true><<<grid, TB, sm, st>>>(a, x, bufX, plan_of<T>(h, 0), phase_of<T>(h, 0), NL); ::vc::note_launch();
-    } else {
-      VC_TRY(set_smem<T>(k_xfwd<T, false>, sm));
-      k_xfwd<T, false><<<grid, TB, sm, st>>>(a, x, bufX, plan_of<T>(h, 0), phase_of<T>(h, 0), NL); ::vc::note_launch();
-    }
+#define VC_XFWD(W)                                                                            \
+  if (adjoint) {                                                                              \
+    VC_TRY(set_smem<T>(k_xfwd<T, true, W>, sm));                                              \
+    k_xfwd<T, true, W><<<grid, TB, sm, st>>>(a, x, bufX, plan_of<T>(h, 0), phase_of<T>(h, 0)); \
+  } else {                                                                                    \
+    VC_TRY(set_smem<T>(k_xfwd<T, false, W>, sm));                                             \
+    k_xfwd<T, false, W><<<grid, TB, sm, st>>>(a, x, bufX, plan_of<T>(h, 0), phase_of<T>(h, 0)); \
+  }
+    VC_TILE_DISPATCH(NL, VC_XFWD)
+#undef VC_XFWD
+    ::vc::note_launch();
     VC_CUDA(cudaGetLastError());
   }
-  // yfwd: bufX [B][GI] -> bufY [B][6] (first GI grids).  The per-item grid
-  // stride differs (6 grids allocated), so launch per batch item block.
+  // yfwd: bufX [B][GI] -> bufY [B][6] (first GI grids)
   const int TXy = smem_lines<T>(g.My, 1, 16);
   {
     size_t sm = (2 * (size_t)g.My * TXy + plan_of<T>(h, 1).twn) * sizeof(C);
-    VC_TRY(set_smem<T>(k_ypass<T, false>, sm));
     dim3 grid((g.Hx + TXy - 1) / TXy, g.Lz, B * GI);
-    k_ypass<T, false><<<grid, TB, sm, st>>>(g, GI, bufX, bufY, (int64_t)GI * gX, (int64_t)6 * gY,
-                                            plan_of<T>(h, 1), phase_of<T>(h, 1), TXy); ::vc::note_launch();
+#define VC_YFWD(W)                                                                          \
+  VC_TRY(set_smem<T>(k_ypass<T, false, W>, sm));                                            \
+  k_ypass<T, false, W><<<grid, TB, sm, st>>>(g, GI, bufX, bufY, (int64_t)GI * gX, (int64_t)6 * gY, \
+                                             plan_of<T>(h, 1), phase_of<T>(h, 1));
+    VC_TILE_DISPATCH(TXy, VC_YFWD)
+#undef VC_YFWD
+    ::vc::note_launch();
     VC_CUDA(cudaGetLastError());
   }
   // zmac
@@ -467,24 +474,30 @@ int mvm(Handle& h, const T* x, T* y, int nrhs, bool adjoint, T* field_out, void*
     const int TXz = smem_lines<T>(g.Mz, 6, 16);
     size_t sm = (2 * (size_t)g.Mz * 6 * TXz + plan_of<T>(h, 2).twn) * sizeof(C);
     dim3 grid(B, (g.Hx + TXz - 1) / TXz, g.My);
-    if (adjoint) {
-      VC_TRY(set_smem<T>(k_zmac<T, true>, sm));
-      k_zmac<T, true><<<grid, TB, sm, st>>>(g, bufY, spec_of<T>(h), plan_of<T>(h, 2),
-                                            phase_of<T>(h, 2), TXz); ::vc::note_launch();
-    } else {
-      VC_TRY(set_smem<T>(k_zmac<T, false>, sm));
-      k_zmac<T, false><<<grid, TB, sm, st>>>(g, bufY, spec_of<T>(h), plan_of<T>(h, 2),
-                                             phase_of<T>(h, 2), TXz); ::vc::note_launch();
-    }
+#define VC_ZMAC(W)                                                                           \
+  if (adjoint) {                                                                             \
+    VC_TRY(set_smem<T>(k_zmac<T, true, W>, sm));                                             \
+    k_zmac<T, true, W><<<grid, TB, sm, st>>>(g, bufY, spec_of<T>(h), plan_of<T>(h, 2), phase_of<T>(h, 2)); \
+  } else {                                                                                   \
+    VC_TRY(set_smem<T>(k_zmac<T, false, W>, sm));                                            \
+    k_zmac<T, false, W><<<grid, TB, sm, st>>>(g, bufY, spec_of<T>(h), plan_of<T>(h, 2), phase_of<T>(h, 2)); \
+  }
+    VC_TILE_DISPATCH(TXz, VC_ZMAC)
+#undef VC_ZMAC
+    ::vc::note_launch();
     VC_CUDA(cudaGetLastError());
   }
   // yinv: bufY [B][6] (first GO grids) -> bufX [B][GO]
   {
     size_t sm = (2 * (size_t)g.My * TXy + plan_of<T>(h, 1).twn) * sizeof(C);
-    VC_TRY(set_smem<T>(k_ypass<T, true>, sm));
     dim3 grid((g.Hx + TXy - 1) / TXy, g.Lz, B * GO);
-    k_ypass<T, true><<<grid, TB, sm, st>>>(g, GO, bufY, bufX, (int64_t)6 * gY, (int64_t)GO * gX,
-                                           plan_of<T>(h, 1), phase_of<T>(h, 1), TXy); ::vc::note_launch();
+#define VC_YINV(W)                                                                         \
+  VC_TRY(set_smem<T>(k_ypass<T, true, W>, sm));                                            \
+  k_ypass<T, true, W><<<grid, TB, sm, st>>>(g, GO, bufY, bufX, (int64_t)6 * gY, (int64_t)GO * gX, \
+                                            plan_of<T>(h, 1), phase_of<T>(h, 1));
+    VC_TILE_DISPATCH(TXy, VC_YINV)
+#undef VC_YINV
+    ::vc::note_launch();
     VC_CUDA(cudaGetLastError());
   }
   // xinv + gather
@@ -493,15 +506,17 @@ int mvm(Handle& h, const T* x, T* y, int nrhs, bool adjoint, T* field_out, void*
     const int lines = adjoint ? (g.Ly + 1) / 2 : g.Ly;
     dim3 grid((lines + NL - 1) / NL, g.Lz, B * 3);
     size_t sm = (2 * (size_t)g.Mx * NL + plan_of<T>(h, 0).twn) * sizeof(C);
-    if (adjoint) {
-      VC_TRY(set_smem<T>(k_xinv<T, true>, sm));
-      k_xinv<T, true><<<grid, TB, sm, st>>>(a, bufX, x, y, field_out, plan_of<T>(h, 0),
-                                            phase_of<T>(h, 0), NL); ::vc::note_launch();
-    } else {
-      VC_TRY(set_smem<T>(k_xinv<T, false>, sm));
-      k_xinv<T, false><<<grid, TB, sm, st>>>(a, bufX, x, y, field_out, plan_of<T>(h, 0),
-                                             phase_of<T>(h, 0), NL); ::vc::note_launch();
-    }
+#define VC_XINV(W)                                                                             \
+  if (adjoint) {                                                                               \
+    VC_TRY(set_smem<T>(k_xinv<T, true, W>, sm));                                               \
+    k_xinv<T, true, W><<<grid, TB, sm, st>>>(a, bufX, x, y, field_out, plan_of<T>(h, 0), phase_of<T>(h, 0)); \
+  } else {                                                                                     \
+    VC_TRY(set_smem<T>(k_xinv<T, false, W>, sm));                                              \
+    k_xinv<T, false, W><<<grid, TB, sm, st>>>(a, bufX, x, y, field_out, plan_of<T>(h, 0), phase_of<T>(h, 0)); \
+  }
+    VC_TILE_DISPATCH(NL, VC_XINV)
+#undef VC_XINV
+    ::vc::note_launch();
     VC_CUDA(cudaGetLastError());
   }
   return VOXCAP_OK;

@@ -161,9 +161,9 @@ static AxisMap axis_map(int kk, int a, int N, int M) {
 
 // ------------------------------------------------------------ generic FFT passes
 // Real rows of length M (x) -> half spectra (Hx), two rows per complex line.
-template <typename T>
+template <typename T, int NL>
 __global__ void k_rows_r2c(const T* __restrict__ in, int64_t nrows, int M, int H,
-                           C_t<T>* __restrict__ out, Plan1D<C_t<T>> plan, int NL) {
+                           C_t<T>* __restrict__ out, Plan1D<C_t<T>> plan) {
   using C = C_t<T>;
   extern __shared__ unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
@@ -179,7 +179,7 @@ __global__ void k_rows_r2c(const T* __restrict__ in, int64_t nrows, int M, int H
     buf[x * NL + l] = mk<C>(a, b);
   }
   __syncthreads();
-  C* res = fft_lines(buf, scr, NL, NL, plan, stw, false);
+  C* res = fft_lines<NL>(buf, scr, NL, plan, stw, false);
   for (int t = threadIdx.x; t < H * NL; t += blockDim.x) {
     int l = t % NL, k = t / NL;
     int64_t ra = row0 + 2 * l, rb = ra + 1;
@@ -194,9 +194,9 @@ __global__ void k_rows_r2c(const T* __restrict__ in, int64_t nrows, int M, int H
 
 // In-place complex FFT along a strided axis of a [outer][L][inner] array;
 // each block handles TX consecutive inner positions of one outer index.
-template <typename T>
+template <typename T, int TX>
 __global__ void k_strided_c2c(C_t<T>* __restrict__ data, int64_t outer, int L, int64_t inner,
-                              Plan1D<C_t<T>> plan, int TX, bool inv) {
+                              Plan1D<C_t<T>> plan, bool inv) {
   using C = C_t<T>;
   extern __shared__ unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
@@ -213,7 +213,7 @@ __global__ void k_strided_c2c(C_t<T>* __restrict__ data, int64_t outer, int L, i
     buf[p * TX + c] = ii < inner ? base[(int64_t)p * inner + ii] : mk<C>((T)0, (T)0);
   }
   __syncthreads();
-  C* res = fft_lines(buf, scr, TX, TX, plan, stw, inv);
+  C* res = fft_lines<TX>(buf, scr, TX, plan, stw, inv);
   for (int t = threadIdx.x; t < L * TX; t += blockDim.x) {
     int c = t % TX, p = t / TX;
     int64_t ii = i0 + c;
@@ -246,12 +246,13 @@ __global__ void k_extract(const double2* __restrict__ spec, Geom g, int kk, bool
   Rf[t] = (float)r;
 }
 
+// largest power-of-two line count (<= maxlines) whose two buffers fit in 96 KB
 template <typename T> static int smem_limit_lines(int L, int maxlines) {
   const size_t budget = 96 * 1024;
   int nl = (int)(budget / (2 * (size_t)L * sizeof(C_t<T>)));
-  if (nl > maxlines) nl = maxlines;
-  if (nl < 1) nl = 1;
-  return nl;
+  int p = 1;
+  while (p * 2 <= nl && p * 2 <= maxlines) p *= 2;
+  return p;
 }
 
 int build_spectra(Handle& h) {
@@ -280,8 +281,12 @@ int build_spectra(Handle& h) {
       int64_t nrows = (int64_t)g.My * g.Mz;
       unsigned nblk = (unsigned)((nrows + 2 * NL - 1) / (2 * NL));
       size_t sm = (2 * (size_t)g.Mx * NL + h.pd[0].twn) * sizeof(double2);
-      VC_CUDA(cudaFuncSetAttribute(k_rows_r2c<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      k_rows_r2c<double><<<nblk, 256, sm, h.stream>>>(circ.p, nrows, g.Mx, g.Hx, spec.p, h.pd[0], NL); ::vc::note_launch();
+#define VC_R2C(W)                                                                                  \
+  VC_CUDA(cudaFuncSetAttribute(k_rows_r2c<double, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)); \
+  k_rows_r2c<double, W><<<nblk, 256, sm, h.stream>>>(circ.p, nrows, g.Mx, g.Hx, spec.p, h.pd[0]);
+      VC_TILE_DISPATCH(NL, VC_R2C)
+#undef VC_R2C
+      ::vc::note_launch();
       VC_CUDA(cudaGetLastError());
     }
     // y: [Mz][My][Hx] along My
@@ -289,9 +294,12 @@ int build_spectra(Handle& h) {
       int TX = smem_limit_lines<double>(g.My, 16);
       int64_t tiles = (g.Hx + TX - 1) / TX;
       size_t sm = (2 * (size_t)g.My * TX + h.pd[1].twn) * sizeof(double2);
-      VC_CUDA(cudaFuncSetAttribute(k_strided_c2c<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      k_strided_c2c<double><<<(unsigned)(g.Mz * tiles), 256, sm, h.stream>>>(
-          spec.p, g.Mz, g.My, g.Hx, h.pd[1], TX, false); ::vc::note_launch();
+#define VC_C2CY(W)                                                                                  \
+  VC_CUDA(cudaFuncSetAttribute(k_strided_c2c<double, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)); \
+  k_strided_c2c<double, W><<<(unsigned)(g.Mz * tiles), 256, sm, h.stream>>>(spec.p, g.Mz, g.My, g.Hx, h.pd[1], false);
+      VC_TILE_DISPATCH(TX, VC_C2CY)
+#undef VC_C2CY
+      ::vc::note_launch();
       VC_CUDA(cudaGetLastError());
     }
     // z: [1][Mz][My*Hx] along Mz
@@ -300,9 +308,12 @@ int build_spectra(Handle& h) {
       int64_t inner = (int64_t)g.My * g.Hx;
       int64_t tiles = (inner + TX - 1) / TX;
       size_t sm = (2 * (size_t)g.Mz * TX + h.pd[2].twn) * sizeof(double2);
-      VC_CUDA(cudaFuncSetAttribute(k_strided_c2c<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      k_strided_c2c<double><<<(unsigned)tiles, 256, sm, h.stream>>>(spec.p, 1, g.Mz, inner, h.pd[2],
-                                                                   TX, false); ::vc::note_launch();
+#define VC_C2CZ(W)                                                                                  \
+  VC_CUDA(cudaFuncSetAttribute(k_strided_c2c<double, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)); \
+  k_strided_c2c<double, W><<<(unsigned)tiles, 256, sm, h.stream>>>(spec.p, 1, g.Mz, inner, h.pd[2], false);
+      VC_TILE_DISPATCH(TX, VC_C2CZ)
+#undef VC_C2CZ
+      ::vc::note_launch();
       VC_CUDA(cudaGetLastError());
     }
     k_extract<<<(unsigned)((Otot + TB - 1) / TB), TB, 0, h.stream>>>(
