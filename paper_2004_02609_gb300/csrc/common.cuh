@@ -13,6 +13,7 @@ void set_error(const std::string& msg);
 // host-side count of kernel launches issued by the library
 void note_launch();
 int64_t launch_count();
+void adjust_launch_count(int64_t delta);
 struct Status {
   int code = VOXCAP_OK;
 };

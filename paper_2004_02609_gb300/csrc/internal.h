@@ -163,6 +163,8 @@ template <typename T>
 int mvm(Handle& h, const T* x, T* y, int nrhs, bool adjoint, T* field_out,
         void* workspace = nullptr);
 size_t mvm_workspace_bytes(const Handle& h, int nrhs, size_t complex_bytes);
+// constant tables and workspace of the product for nrhs columns
+int mvm_prepare(Handle& h, int nrhs, size_t complex_bytes);
 template <typename T>
 int precond_apply(Handle& h, const T* r, T* z, int nrhs);
 int solve(Handle& h, const double* B, int nrhs, double tol, double* X, voxcap_stats* st,

@@ -525,6 +525,11 @@ int mvm(Handle& h, const T* x, T* y, int nrhs, bool adjoint, T* field_out, void*
 template int mvm<float>(Handle&, const float*, float*, int, bool, float*, void*);
 template int mvm<double>(Handle&, const double*, double*, int, bool, double*, void*);
 
+int mvm_prepare(Handle& h, int nrhs, size_t complex_bytes) {
+  VC_TRY(ensure_sign_tables());
+  return h.ws.alloc(mvm_workspace_bytes(h, nrhs, complex_bytes));
+}
+
 // bytes of scratch one product over nrhs columns needs (x-pass and y/z-pass
 // intermediates of every batch item)
 size_t mvm_workspace_bytes(const Handle& h, int nrhs, size_t complex_bytes) {

@@ -165,6 +165,16 @@ __global__ void k_cycle_start(GState s, int nrhs, int m, bool first, double* inv
   inv_norm[col] = beta > 0.0 ? 1.0 / beta : 0.0;
 }
 
+// after a cycle: a column is unconverged if its residual estimate is above
+// rtol * beta0 and it has iterations left; mark it active for the next cycle
+__global__ void k_reactivate(GState s, int nrhs, int m, double rtol, int max_it) {
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= nrhs) return;
+  const int k = s.kused[col];
+  const double res = fabs(s.g[(int64_t)col * (m + 1) + k]);
+  s.active[col] = (s.beta0[col] > 0.0 && res > rtol * s.beta0[col] && s.iters[col] < max_it) ? 1 : 0;
+}
+
 // y = H^-1 g (upper triangular, k x k), stored in hcol
 __global__ void k_backsolve(GState s, int nrhs, int m) {
   const int col = blockIdx.x * blockDim.x + threadIdx.x;
@@ -228,8 +238,114 @@ static int nchunks_for(int64_t N) {
   return (int)c;
 }
 
+// ---- kernels of the graph-captured Arnoldi step (iteration index on the device) ----
+// One CGS pass over the basis V[0..j] (j = *jdev): optionally w -= sum_i coef_i V_i,
+// then partial dots with V_i (dot) or ||w||^2 (norm).
+template <typename T>
+__global__ void k_gs_dev(const T* __restrict__ V, T* __restrict__ w, int64_t N, int nrhs, bool update,
+                         const double* __restrict__ coef, int coef_ld, bool dot, const int* __restrict__ jdev,
+                         const int* __restrict__ active, int nchunks, double* __restrict__ partial, int part_ld) {
+  const int col = blockIdx.y;
+  const int chunk = blockIdx.x;
+  if (!active[col]) return;
+  const int nv = *jdev + 1;
+  const int64_t per = (N + nchunks - 1) / nchunks;
+  const int64_t lo = chunk * per, hi = min(N, lo + per);
+  T* wc = w + (int64_t)col * N;
+  const int64_t vstride = (int64_t)nrhs * N;
+  if (update) {
+    for (int64_t p = lo + threadIdx.x; p < hi; p += blockDim.x) {
+      double acc = (double)wc[p];
+      for (int i = 0; i < nv; ++i)
+        acc -= coef[(int64_t)col * coef_ld + i] * (double)V[i * vstride + (int64_t)col * N + p];
+      wc[p] = (T)acc;
+    }
+    __syncthreads();
+  }
+  const int nd = dot ? nv : 1;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = wid; i < nd; i += nw) {
+    const T* vi = dot ? V + i * vstride + (int64_t)col * N : wc;
+    double acc = 0.0;
+    for (int64_t p = lo + lane; p < hi; p += 32) acc += (double)vi[p] * (double)wc[p];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) partial[((int64_t)col * part_ld + i) * nchunks + chunk] = acc;
+  }
+}
+
+// out[col][i] = sum_chunk partial[col][i][chunk], i < (*jdev + 1) (dot) or i = 0 (norm)
+__global__ void k_reduce_dev(const double* __restrict__ partial, int nchunks, bool dot, const int* __restrict__ jdev,
+                             int part_ld, const int* __restrict__ active, double* __restrict__ out, int out_ld) {
+  __shared__ double sh[32];
+  const int col = blockIdx.y, i = blockIdx.x;
+  if (!active[col]) return;
+  if (i >= (dot ? *jdev + 1 : 1)) return;
+  double acc = 0.0;
+  for (int c = threadIdx.x; c < nchunks; c += blockDim.x) acc += partial[((int64_t)col * part_ld + i) * nchunks + c];
+  double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) out[(int64_t)col * out_ld + i] = s;
+}
+
+__global__ void k_givens_dev(GState s, int nrhs, int m, const int* __restrict__ jdev, double rtol, int max_it,
+                             double* inv_norm) {
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= nrhs) return;
+  const int j = *jdev;
+  if (!s.active[col] || j >= m) { inv_norm[col] = 0.0; return; }
+  double* H = s.H + (int64_t)col * (m + 1) * m + (int64_t)j * (m + 1);
+  double* cs = s.cs + (int64_t)col * m;
+  double* sn = s.sn + (int64_t)col * m;
+  double* g = s.g + (int64_t)col * (m + 1);
+  for (int i = 0; i <= j; ++i) H[i] = s.hcol[(int64_t)col * (m + 1) + i] + s.hcol2[(int64_t)col * (m + 1) + i];
+  double hn = sqrt(fmax(s.nrm2[col], 0.0));
+  H[j + 1] = hn;
+  for (int i = 0; i < j; ++i) {
+    double t = cs[i] * H[i] + sn[i] * H[i + 1];
+    H[i + 1] = -sn[i] * H[i] + cs[i] * H[i + 1];
+    H[i] = t;
+  }
+  double den = hypot(H[j], H[j + 1]);
+  double c = den > 0.0 ? H[j] / den : 1.0;
+  double sv = den > 0.0 ? H[j + 1] / den : 0.0;
+  cs[j] = c;
+  sn[j] = sv;
+  H[j] = den;
+  H[j + 1] = 0.0;
+  g[j + 1] = -sv * g[j];
+  g[j] = c * g[j];
+  s.kused[col] = j + 1;
+  s.iters[col] += 1;
+  const bool conv = fabs(g[j + 1]) <= rtol * s.beta0[col];
+  if (conv || hn == 0.0 || s.iters[col] >= max_it || j + 1 >= m) s.active[col] = 0;
+  inv_norm[col] = hn > 0.0 ? 1.0 / hn : 0.0;
+}
+
+// V[j+1] = w * invn and vcur = V[j+1] for the columns still iterating; then j += 1
+template <typename T>
+__global__ void k_store_next(const T* __restrict__ w, T* __restrict__ V, T* __restrict__ vcur, int64_t N, int nrhs,
+                             const int* __restrict__ jdev, int m, const double* __restrict__ invn,
+                             const int* __restrict__ kused, int* __restrict__ jnext) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = *jdev;
+  if (t < N * nrhs && j < m) {
+    const int col = (int)(t / N);
+    if (kused[col] == j + 1) {          // this column took step j
+      const T v = (T)((double)w[t] * invn[col]);
+      V[(int64_t)(j + 1) * N * nrhs + t] = v;
+      vcur[t] = v;
+    }
+  }
+  if (t == 0) *jnext = j + 1;
+}
+
+__global__ void k_copy_j(const int* __restrict__ src, int* __restrict__ dst) { *dst = *src; }
+
 // Solve R A d = R r (x0 = 0) per column to a preconditioned relative
-// residual rtol.  r, d: device [nrhs][N] in T.  `adjoint`: use A^T and R^T.
+// residual rtol.  r, d: device [nrhs][N] in T.  `adjoint`: use A^T.
+// One Arnoldi step (product, preconditioner, two Gram-Schmidt passes,
+// Givens update, next basis vector) is captured once as a CUDA graph whose
+// kernels read the step index from device memory; the host launches it
+// speculatively one step ahead of the convergence flags it reads back.
 template <typename T>
 static int gmres(Handle& h, const T* r, T* d, int nrhs, double rtol, int max_it, bool adjoint,
                  SolveCounters* cnt) {
@@ -237,17 +353,18 @@ static int gmres(Handle& h, const T* r, T* d, int nrhs, double rtol, int max_it,
   const int m = std::max(1, h.opts.restart);
   cudaStream_t st = h.stream;
   const int nch = nchunks_for(N);
-  // workspace
   const size_t nV = (size_t)(m + 1) * nrhs * N;
   const size_t nW = (size_t)nrhs * N;
-  size_t bytes = sizeof(T) * (nV + nW);
+  size_t bytes = sizeof(T) * (nV + 3 * nW) + 256;
   const size_t nd_H = (size_t)nrhs * (m + 1) * m, nd_cs = (size_t)nrhs * m, nd_g = (size_t)nrhs * (m + 1);
   const size_t ndbl = nd_H + 2 * nd_cs + 3 * nd_g + 3 * (size_t)nrhs + (size_t)nrhs * (m + 1) * nch;
-  bytes += sizeof(double) * ndbl + sizeof(int) * 3 * nrhs + 256;
+  bytes += sizeof(double) * ndbl + sizeof(int) * (3 * nrhs + 4) + 256;
   VC_TRY(h.solver_ws.alloc(bytes));
   char* wp = h.solver_ws.p;
   T* V = reinterpret_cast<T*>(wp); wp += sizeof(T) * nV;
   T* W = reinterpret_cast<T*>(wp); wp += sizeof(T) * nW;
+  T* W2 = reinterpret_cast<T*>(wp); wp += sizeof(T) * nW;
+  T* vcur = reinterpret_cast<T*>(wp); wp += sizeof(T) * nW;
   wp = reinterpret_cast<char*>(((uintptr_t)wp + 15) & ~(uintptr_t)15);
   double* dp = reinterpret_cast<double*>(wp);
   GState s;
@@ -265,85 +382,141 @@ static int gmres(Handle& h, const T* r, T* d, int nrhs, double rtol, int max_it,
   s.active = ip; ip += nrhs;
   s.kused = ip; ip += nrhs;
   s.iters = ip; ip += nrhs;
+  int* jdev = ip; ip += 1;
+  int* jnext = ip; ip += 1;
   VC_CUDA(cudaMemsetAsync(d, 0, sizeof(T) * nW, st));
   const int TB = 256;
   const unsigned gN = (unsigned)((N * nrhs + TB - 1) / TB);
   const unsigned gC = (unsigned)((nrhs + 63) / 64);
-  std::vector<int> act(nrhs);
+  // the product's tables and workspace must exist before capture (no
+  // allocation or symbol copy inside the graph)
+  VC_TRY(mvm_prepare(h, nrhs, sizeof(C_t<T>)));
+  const int64_t launches_before_capture = launch_count();
+
+  // ---- capture one Arnoldi step ----
+  cudaStream_t cap = nullptr;
+  VC_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  {
+    const cudaStream_t saved = h.stream;
+    h.stream = cap;
+    int rc = VOXCAP_OK;
+    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed) != cudaSuccess) rc = VOXCAP_ERR_CUDA;
+    if (rc == VOXCAP_OK) rc = mvm<T>(h, vcur, W, nrhs, adjoint, nullptr);
+    if (rc == VOXCAP_OK) rc = precond_apply<T>(h, W, W2, nrhs);
+    if (rc == VOXCAP_OK) {
+      dim3 gsw(nch, nrhs), grd(m + 1, nrhs);
+      k_gs_dev<T><<<gsw, kDotTB, 0, cap>>>(V, W2, N, nrhs, false, nullptr, 0, true, jdev, s.active, nch, partial, m + 1);
+      k_reduce_dev<<<grd, kDotTB, 0, cap>>>(partial, nch, true, jdev, m + 1, s.active, s.hcol, m + 1);
+      k_gs_dev<T><<<gsw, kDotTB, 0, cap>>>(V, W2, N, nrhs, true, s.hcol, m + 1, true, jdev, s.active, nch, partial, m + 1);
+      k_reduce_dev<<<grd, kDotTB, 0, cap>>>(partial, nch, true, jdev, m + 1, s.active, s.hcol2, m + 1);
+      k_gs_dev<T><<<gsw, kDotTB, 0, cap>>>(V, W2, N, nrhs, true, s.hcol2, m + 1, false, jdev, s.active, nch, partial, m + 1);
+      k_reduce_dev<<<dim3(1, nrhs), kDotTB, 0, cap>>>(partial, nch, false, jdev, m + 1, s.active, s.nrm2, 1);
+      k_givens_dev<<<gC, 64, 0, cap>>>(s, nrhs, m, jdev, rtol, max_it, invn);
+      k_store_next<T><<<gN, TB, 0, cap>>>(W2, V, vcur, N, nrhs, jdev, m, invn, s.kused, jnext);
+      k_copy_j<<<1, 1, 0, cap>>>(jnext, jdev);
+    }
+    cudaError_t ce = cudaStreamEndCapture(cap, &graph);
+    h.stream = saved;
+    if (rc == VOXCAP_OK && ce != cudaSuccess) rc = VOXCAP_ERR_CUDA;
+    if (rc == VOXCAP_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) rc = VOXCAP_ERR_CUDA;
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cap);
+    adjust_launch_count(launches_before_capture - launch_count());   // capture issued no launch
+    if (rc != VOXCAP_OK) {
+      if (exec) cudaGraphExecDestroy(exec);
+      (void)cudaGetLastError();
+      set_error("capture of the GMRES step failed");
+      return rc;
+    }
+  }
+  struct ExecGuard {
+    cudaGraphExec_t e;
+    ~ExecGuard() { if (e) cudaGraphExecDestroy(e); }
+  } guard{exec};
+  // kernel launches inside one step (counted per replay)
+  const int step_launches = 5 + ((h.pre.kind == VOXCAP_PRECOND_BDD || h.pre.kind == VOXCAP_PRECOND_BD) &&
+                                 h.pre.nblocks > 0 && h.pre.max_n > 0 ? 2 : 1) + 9;
+
+  int* act_h = nullptr;
+  VC_CUDA(cudaMallocHost(&act_h, sizeof(int) * 2 * nrhs));
+  struct HostGuard {
+    int* p;
+    ~HostGuard() { if (p) cudaFreeHost(p); }
+  } hguard{act_h};
+  cudaEvent_t ev[2];
+  VC_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+  VC_CUDA(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+  struct EvGuard {
+    cudaEvent_t* e;
+    ~EvGuard() { cudaEventDestroy(e[0]); cudaEventDestroy(e[1]); }
+  } eguard{ev};
+
   bool first = true;
-  auto apply_RA = [&](const T* in, T* out) -> int {
-    VC_TRY(mvm<T>(h, in, W, nrhs, adjoint, nullptr));
-    cnt->matvecs += 1;
-    // the transposed solve is preconditioned by the same R: any nonsingular R
-    // leaves the solution unchanged, and for BDD (symmetric conductor blocks,
-    // diagonal dielectric part) R^T = R exactly
-    VC_TRY(precond_apply<T>(h, W, out, nrhs));
-    return VOXCAP_OK;
-  };
   int total_it = 0;
+  std::vector<int> its(nrhs);
   for (int cycle = 0; cycle < 100000; ++cycle) {
-    // V0 = R (r - A d)
+    // V0 = R (r - A d), vcur = V0 / ||V0||, j = 0
     if (first) {
       VC_TRY(precond_apply<T>(h, r, V, nrhs));
     } else {
       VC_TRY(mvm<T>(h, d, W, nrhs, adjoint, nullptr));
       cnt->matvecs += 1;
-      T* tmp = V + (size_t)m * nrhs * N;    // last basis slot as scratch
-      k_sub<T><<<gN, TB, 0, st>>>(r, W, tmp, N * nrhs); ::vc::note_launch();
-      VC_TRY(precond_apply<T>(h, tmp, V, nrhs));
+      k_sub<T><<<gN, TB, 0, st>>>(r, W, W2, N * nrhs); ::vc::note_launch();
+      VC_TRY(precond_apply<T>(h, W2, V, nrhs));
     }
     dim3 gsw(nch, nrhs);
-    k_gs_sweep<T><<<gsw, kDotTB, 0, st>>>(V, V, N, nrhs, 0, nullptr, 0, 0, true, nullptr, nch,
-                                          partial, m + 1); ::vc::note_launch();
+    k_gs_sweep<T><<<gsw, kDotTB, 0, st>>>(V, V, N, nrhs, 0, nullptr, 0, 0, true, nullptr, nch, partial, m + 1); ::vc::note_launch();
     k_reduce_partial<<<dim3(1, nrhs), kDotTB, 0, st>>>(partial, nch, 1, m + 1, nullptr, s.nrm2, 1, false); ::vc::note_launch();
     k_cycle_start<<<gC, 64, 0, st>>>(s, nrhs, m, first, invn); ::vc::note_launch();
     k_scale_cols<T><<<gN, TB, 0, st>>>(V, N, nrhs, invn, nullptr); ::vc::note_launch();
+    VC_CUDA(cudaMemcpyAsync(vcur, V, sizeof(T) * nW, cudaMemcpyDeviceToDevice, st));
+    VC_CUDA(cudaMemsetAsync(jdev, 0, sizeof(int), st));
     VC_CUDA(cudaGetLastError());
     first = false;
-    int j = 0;
-    for (j = 0; j < m; ++j) {
-      T* vj = V + (size_t)j * nrhs * N;
-      T* w = V + (size_t)(j + 1) * nrhs * N;
-      VC_TRY(apply_RA(vj, w));
-      // pass 1: h = V^T w
-      k_gs_sweep<T><<<gsw, kDotTB, 0, st>>>(V, w, N, nrhs, 0, nullptr, 0, j + 1, false, s.active, nch,
-                                            partial, m + 1); ::vc::note_launch();
-      k_reduce_partial<<<dim3(j + 1, nrhs), kDotTB, 0, st>>>(partial, nch, j + 1, m + 1, s.active,
-                                                             s.hcol, m + 1, false); ::vc::note_launch();
-      // pass 2: w -= V h ; h2 = V^T w
-      k_gs_sweep<T><<<gsw, kDotTB, 0, st>>>(V, w, N, nrhs, j + 1, s.hcol, m + 1, j + 1, false, s.active,
-                                            nch, partial, m + 1); ::vc::note_launch();
-      k_reduce_partial<<<dim3(j + 1, nrhs), kDotTB, 0, st>>>(partial, nch, j + 1, m + 1, s.active,
-                                                             s.hcol2, m + 1, false); ::vc::note_launch();
-      // w -= V h2 ; ||w||^2
-      k_gs_sweep<T><<<gsw, kDotTB, 0, st>>>(V, w, N, nrhs, j + 1, s.hcol2, m + 1, 0, true, s.active,
-                                            nch, partial, m + 1); ::vc::note_launch();
-      k_reduce_partial<<<dim3(1, nrhs), kDotTB, 0, st>>>(partial, nch, 1, m + 1, s.active, s.nrm2, 1,
-                                                         false); ::vc::note_launch();
-      k_givens<<<gC, 64, 0, st>>>(s, nrhs, m, j, rtol, max_it, invn); ::vc::note_launch();
-      k_scale_cols<T><<<gN, TB, 0, st>>>(w, N, nrhs, invn, nullptr); ::vc::note_launch();
-      VC_CUDA(cudaGetLastError());
-      ++total_it;
-      VC_CUDA(cudaMemcpyAsync(act.data(), s.active, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
-      VC_CUDA(cudaStreamSynchronize(st));
+    // Arnoldi steps: launch step j+1 before reading the flags of step j
+    int launched = 0, checked = 0;
+    bool done = false;
+    auto launch_step = [&]() -> int {
+      VC_CUDA(cudaGraphLaunch(exec, st));
+      for (int q = 0; q < step_launches; ++q) ::vc::note_launch();
+      cnt->matvecs += 1;
+      VC_CUDA(cudaMemcpyAsync(act_h + (launched & 1) * nrhs, s.active, sizeof(int) * nrhs,
+                              cudaMemcpyDeviceToHost, st));
+      VC_CUDA(cudaEventRecord(ev[launched & 1], st));
+      ++launched;
+      return VOXCAP_OK;
+    };
+    VC_TRY(launch_step());
+    while (!done) {
+      if (launched < m) VC_TRY(launch_step());
+      VC_CUDA(cudaEventSynchronize(ev[checked & 1]));
+      const int* a = act_h + (checked & 1) * nrhs;
+      ++checked;
       bool any = false;
-      for (int c = 0; c < nrhs; ++c) any = any || act[c];
-      if (!any) { ++j; break; }
+      for (int c = 0; c < nrhs; ++c) any = any || a[c];
+      if (!any || checked >= m) done = true;
     }
+    total_it += checked;
+    VC_CUDA(cudaStreamSynchronize(st));
     k_backsolve<<<gC, 64, 0, st>>>(s, nrhs, m); ::vc::note_launch();
     k_update_x<T><<<gN, TB, 0, st>>>(d, V, N, nrhs, s.hcol, s.kused, m); ::vc::note_launch();
     VC_CUDA(cudaGetLastError());
-    // finished?
-    VC_CUDA(cudaMemcpyAsync(act.data(), s.active, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
-    std::vector<int> its(nrhs);
+    // columns still unconverged after a full cycle restart; converged ones stay inactive
     VC_CUDA(cudaMemcpyAsync(its.data(), s.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
     VC_CUDA(cudaStreamSynchronize(st));
-    bool any = false;
     int maxit = 0;
-    for (int c = 0; c < nrhs; ++c) { any = any || act[c]; maxit = std::max(maxit, its[c]); }
+    for (int c = 0; c < nrhs; ++c) maxit = std::max(maxit, its[c]);
+    // a column that stopped only because the cycle ended is still unconverged:
+    // re-activate it from the residual estimate
+    k_reactivate<<<gC, 64, 0, st>>>(s, nrhs, m, rtol, max_it); ::vc::note_launch();
+    std::vector<int> act(nrhs);
+    VC_CUDA(cudaMemcpyAsync(act.data(), s.active, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
+    VC_CUDA(cudaStreamSynchronize(st));
+    bool any = false;
+    for (int c = 0; c < nrhs; ++c) any = any || act[c];
     if (!any || maxit >= max_it) break;
-    // restart: the next cycle recomputes the residual of the active columns;
-    // converged columns keep active = 0 (k_cycle_start leaves it alone)
   }
   cnt->iters += total_it;
   return VOXCAP_OK;

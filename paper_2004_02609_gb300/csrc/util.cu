@@ -32,6 +32,7 @@ cudaStream_t alloc_stream() { return g_alloc_stream; }
 static std::atomic<int64_t> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+void adjust_launch_count(int64_t delta) { g_launches.fetch_add(delta, std::memory_order_relaxed); }
 
 // Factor L into radices {8,4,2,3,5,7}; returns false if L has another prime factor.
 bool factor_length(int L, int* radix, int* nst) {
