@@ -269,6 +269,34 @@ def run_ours(args, rank, world):
     return res
 
 
+def run_products(args):
+    """Product-only timing (--products): setup once, then K batched FP32
+    products with all conductor columns; used for kernel profiling."""
+    import torch
+    import __graft_entry__ as ge
+    from paper_2004_02609_gb300 import voxcap as V
+    ge.build()
+    w, desc = workload(args.workload)
+    vc = V.VoxCap(torch.tensor(w.labels, device="cuda"), w.conductor_id, w.eps_r, w.voxel_size)
+    m = vc.n_conductors
+    x = torch.randn(m, vc.N, device="cuda", dtype=torch.float32)
+    for _ in range(args.warmup):
+        vc.matvec(x)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        vc.matvec(x)
+    e1.record()
+    e1.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / args.steps
+    hbm, src = read_peaks()
+    b = mvm_model_bytes(vc, m) * m
+    return {"mode": "products", "workload": desc, "panels": vc.N, "columns": m,
+            "fft_lengths": vc.fft_lengths(), "s_per_batched_product": t, "matvecs_per_s": m / t,
+            "model_bytes": b, "achieved_GBps": b / t / 1e9, "frac_of_" + src + "_hbm": b / t / 1e9 / hbm}
+
+
 def cpu_baseline(w, budget_s=20.0):
     """The oracle as it stands on the host cores, on a bounded sample: the
     dense assembly integrates every distinct panel-pair integral; a random
@@ -352,7 +380,12 @@ def main():
     ap.add_argument("--workload", default="plates")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--products", action="store_true",
+                    help="time only the batched FP32 products of the workload (profiling aid)")
     args = ap.parse_args()
+    if args.products:
+        print(json.dumps(run_products(args)), flush=True)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if world > 1:
