@@ -102,8 +102,11 @@ typedef struct voxcap_opts {
   int max_sweeps;      /* cap on refinement sweeps (default 20) */
   int nv[3];           /* small-box size of the preconditioner in voxels (default 10, Sec. II.D) */
   int precond;         /* VOXCAP_PRECOND_* (default BDD) */
-  int pad_mode;        /* 0: smallest even 2/3/5/7-smooth M >= 2N+1 per axis (default);
-                          1: the paper's M = 2(N+1) (must be 2/3/5/7-smooth) */
+  int pad_mode;        /* padded FFT length per axis, all >= 2N+1 (Appendix B):
+                          0: the cheapest even 2/3/5/7-smooth length within 25% by
+                             the FFT engine's cost model (default);
+                          1: the paper's M = 2(N+1) (must be 2/3/5/7-smooth);
+                          2: the smallest even 2/3/5/7-smooth length */
   const voxcap_tucker* tucker; /* NULL: generate the Toeplitz tensors in FP64 (Eqs. 5-6);
                           else restore them from these Tucker factors on the
                           tensor cores (Sec. II.C), cropped to the grid */

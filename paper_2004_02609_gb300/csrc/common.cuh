@@ -82,7 +82,7 @@ __device__ __forceinline__ uint32_t fdiv(uint32_t x, const FastDiv& f) {
   return f.d <= 1 ? x : __umulhi(x, f.m);
 }
 
-// A 1-D transform of length L factored into radices r[0..nst) in {2,3,4,5,7,8}.
+// A 1-D transform of length L factored into radices r[0..nst) in {2,3,4,5,7,8,9,16}.
 // Stage s combines sub-transforms of length Ns[s] with radix[s]; its twiddles
 // exp(-2 pi i r k / (Ns R)), k < Ns, 1 <= r < R, sit at stw[twoff[s] + k (R-1) + r - 1].
 template <typename C> struct Plan1D {
@@ -97,6 +97,7 @@ template <typename C> struct Plan1D {
 };
 
 bool factor_length(int L, int* radix, int* nst);   // host: false if not 2/3/5/7-smooth
+double fft_cost(int L);                           // host: relative cost of one padded length
 
 // Copy the stage twiddles of a plan into shared memory (caller synchronises).
 template <typename C> __device__ __forceinline__ void load_twiddles(C* dst, const Plan1D<C>& p) {
@@ -157,6 +158,47 @@ template <int R, typename C> __device__ __forceinline__ void dft(C* v, bool inv)
     v[1] = cadd(t1, u1); v[6] = csub(t1, u1);
     v[2] = cadd(t2, u2); v[5] = csub(t2, u2);
     v[3] = cadd(t3, u3); v[4] = csub(t3, u3);
+  } else if constexpr (R == 9 || R == 16) {
+    // R = Q * Q (Q = 3 or 4): X[q + Q p] = sum_k1 wQ^(k1 p) [ wR^(k1 q) sum_n2 x[k1 + Q n2] wQ^(n2 q) ]
+    constexpr int Q = R == 9 ? 3 : 4;
+    C a[Q][Q];
+#pragma unroll
+    for (int k1 = 0; k1 < Q; ++k1) {
+#pragma unroll
+      for (int n2 = 0; n2 < Q; ++n2) a[k1][n2] = v[k1 + Q * n2];
+      dft<Q, C>(a[k1], inv);
+    }
+#pragma unroll
+    for (int k1 = 1; k1 < Q; ++k1)
+#pragma unroll
+      for (int q = 1; q < Q; ++q) {
+        const int mm = k1 * q;                     // exponent of wR
+        T wr, wi;
+        if constexpr (R == 16) {
+          wr = mm == 1 ? (T)0.9238795325112867561282 : mm == 2 ? (T)0.7071067811865475244008
+             : mm == 3 ? (T)0.3826834323650897717285 : mm == 4 ? (T)0.0
+             : mm == 6 ? (T)-0.7071067811865475244008 : (T)-0.9238795325112867561282;
+          wi = mm == 1 ? (T)-0.3826834323650897717285 : mm == 2 ? (T)-0.7071067811865475244008
+             : mm == 3 ? (T)-0.9238795325112867561282 : mm == 4 ? (T)-1.0
+             : mm == 6 ? (T)-0.7071067811865475244008 : (T)0.3826834323650897717285;
+        } else {
+          wr = mm == 1 ? (T)0.7660444431189780352024 : mm == 2 ? (T)0.1736481776669303488517
+                                                     : (T)-0.9396926207859083840541;
+          wi = mm == 1 ? (T)-0.6427876096865393263226 : mm == 2 ? (T)-0.9848077530122080593667
+                                                     : (T)-0.3420201433256687330441;
+        }
+        if (inv) wi = -wi;
+        a[k1][q] = cmul(a[k1][q], mk<C>(wr, wi));
+      }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      C b[Q];
+#pragma unroll
+      for (int k1 = 0; k1 < Q; ++k1) b[k1] = a[k1][q];
+      dft<Q, C>(b, inv);
+#pragma unroll
+      for (int p = 0; p < Q; ++p) v[q + Q * p] = b[p];
+    }
   } else {   // R == 8: two radix-4 halves
     using TT = T;
     C e[4] = {v[0], v[2], v[4], v[6]};
@@ -224,6 +266,8 @@ __device__ C* fft_lines(C* buf, C* scr, int ld, const Plan1D<C>& p, const C* stw
       case 4: stockham_stage<4, NL, C>(src, dst, p.L, p.Ns[s], p.fNs[s], ld, tw, inv); break;
       case 5: stockham_stage<5, NL, C>(src, dst, p.L, p.Ns[s], p.fNs[s], ld, tw, inv); break;
       case 7: stockham_stage<7, NL, C>(src, dst, p.L, p.Ns[s], p.fNs[s], ld, tw, inv); break;
+      case 9: stockham_stage<9, NL, C>(src, dst, p.L, p.Ns[s], p.fNs[s], ld, tw, inv); break;
+      case 16: stockham_stage<16, NL, C>(src, dst, p.L, p.Ns[s], p.fNs[s], ld, tw, inv); break;
       default: stockham_stage<8, NL, C>(src, dst, p.L, p.Ns[s], p.fNs[s], ld, tw, inv); break;
     }
     __syncthreads();

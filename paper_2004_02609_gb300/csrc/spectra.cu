@@ -27,12 +27,28 @@ static bool smooth7(int n) {
   return n == 1;
 }
 
+// Padded length along an axis: the paper's 2(N+1) (mode 1), or the cheapest
+// even 2/3/5/7-smooth length >= 2N+1 within 25% of it by the FFT cost model.
 static int pick_length(int N, int mode) {
   if (mode == 1) return 2 * (N + 1);
-  int m = 2 * N + 1;
-  if (m & 1) ++m;
-  while (!smooth7(m)) m += 2;
-  return m;
+  int lo = 2 * N + 1;
+  if (lo & 1) ++lo;
+  if (mode == 2) {                       // smallest even smooth length
+    while (!smooth7(lo)) lo += 2;
+    return lo;
+  }
+  int best = -1;
+  double bc = 1e300;
+  for (int m = lo; m <= lo + lo / 4 + 2; m += 2) {
+    if (!smooth7(m)) continue;
+    const double c = fft_cost(m);
+    if (c < bc) { bc = c; best = m; }
+  }
+  if (best < 0) {
+    best = lo;
+    while (!smooth7(best)) best += 2;
+  }
+  return best;
 }
 
 // Stage twiddles of a radix plan (see Plan1D) and the half-voxel phases

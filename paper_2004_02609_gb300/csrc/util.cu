@@ -34,18 +34,43 @@ void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 void adjust_launch_count(int64_t delta) { g_launches.fetch_add(delta, std::memory_order_relaxed); }
 
-// Factor L into radices {8,4,2,3,5,7}; returns false if L has another prime factor.
+// Factor L into radices: 16, 8, 4, 2 for the powers of two, 9, 3, 5, 7 for
+// the odd part; returns false if L has another prime factor.
 bool factor_length(int L, int* radix, int* nst) {
   int n = 0;
   int r = L;
   if (L < 1) return false;
+  while (r % 16 == 0 && n < kMaxStages) { radix[n++] = 16; r /= 16; }
   while (r % 8 == 0 && n < kMaxStages) { radix[n++] = 8; r /= 8; }
   while (r % 4 == 0 && n < kMaxStages) { radix[n++] = 4; r /= 4; }
   while (r % 2 == 0 && n < kMaxStages) { radix[n++] = 2; r /= 2; }
+  while (r % 9 == 0 && n < kMaxStages) { radix[n++] = 9; r /= 9; }
   for (int p : {3, 5, 7})
     while (r % p == 0 && n < kMaxStages) { radix[n++] = p; r /= p; }
   *nst = n;
   return r == 1;
+}
+
+// Relative cost of transforming along an axis of padded length L: every
+// stage is one shared-memory round trip plus its butterfly work, and two
+// round trips' worth of memory traffic per point come on top.
+double fft_cost(int L) {
+  int rad[kMaxStages], nst = 0;
+  if (!factor_length(L, rad, &nst)) return 1e300;
+  double c = 2.0;
+  for (int s = 0; s < nst; ++s) {
+    switch (rad[s]) {
+      case 2: c += 1.3; break;
+      case 3: c += 1.5; break;
+      case 4: c += 1.4; break;
+      case 5: c += 1.8; break;
+      case 7: c += 2.2; break;
+      case 8: c += 1.6; break;
+      case 9: c += 1.9; break;
+      default: c += 1.8; break;   // 16
+    }
+  }
+  return c * (double)L;
 }
 
 // ---------------------------------------------------------------- scan

@@ -127,7 +127,7 @@ def test_toeplitz_tables_sampled():
 
 
 @pytest.mark.parametrize("w", SMALL[1:4] + [SMALL[5]], ids=lambda w: w.name)
-@pytest.mark.parametrize("pad_mode", [0, 1])
+@pytest.mark.parametrize("pad_mode", [0, 1, 2])
 def test_matvec_matches_dense(w, pad_mode):
     import torch
     nx, ny, nz = w.shape_xyz
@@ -156,12 +156,12 @@ def test_matvec_matches_dense(w, pad_mode):
 @pytest.mark.parametrize("shape", [(6, 4, 5), (12, 3, 17), (24, 10, 6)])
 def test_matvec_every_radix(shape):
     """Grids whose padded lengths need every radix of the FFT engine
-    (14, 10, 12 / 28, 8, 36 / 50, 24, 14 = 2,3,4,5,7,8 factors): forward and
-    transposed products against the dense oracle, FP64 and FP32."""
+    (16, 10, 12 / 28, 8, 36 / 56, 24, 16: factors 2, 3, 4, 5, 7, 8, 9, 16):
+    forward and transposed products against the dense oracle, FP64 and FP32."""
     import torch
     w = W.random_structure(shape, 9, n_cond=2)
     vc = make(w)
-    radices = {p for M in vc.fft_lengths() for p in (2, 3, 5, 7) if M % p == 0}
+    radices = {p for M in vc.fft_lengths() for p in (2, 3, 5, 7, 9, 16) if M % p == 0}
     ps, A = dense(w)
     X = np.random.default_rng(3).standard_normal((2, ps.n))
     x64 = torch.tensor(X, device="cuda")
