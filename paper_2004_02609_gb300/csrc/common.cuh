@@ -276,6 +276,56 @@ __device__ C* fft_lines(C* buf, C* scr, int ld, const Plan1D<C>& p, const C* stw
   return src;
 }
 
+// One Stockham stage over `nlines` lines whose inputs come from ld(line, pos)
+// and whose outputs go to st(line, pos, value), so that a pass can read its
+// first stage straight from global memory and write its last stage straight
+// back.  Requires nb * nlines < 2^16 (nb = L / R).
+template <int R, typename C, typename Ld, typename St>
+__device__ __forceinline__ void stockham_stage_io(int L, int Ns, const FastDiv& fNs, int nlines,
+                                                  const FastDiv& fnl, const C* __restrict__ tw,
+                                                  bool inv, Ld ld, St st) {
+  const int nb = L / R;
+  const int total = nb * nlines;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int j = (int)fdiv((uint32_t)t, fnl);
+    const int line = t - j * nlines;
+    const int k = j - (int)fdiv((uint32_t)j, fNs) * Ns;
+    C v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = ld(line, j + r * nb);
+    if (Ns > 1) {
+      const C* w = tw + k * (R - 1);
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        C ww = w[r - 1];
+        if (inv) ww.y = -ww.y;
+        v[r] = cmul(v[r], ww);
+      }
+    }
+    dft<R, C>(v, inv);
+    const int base = (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) st(line, base + r * Ns, v[r]);
+  }
+}
+
+// Stage s of plan p through stockham_stage_io (stw: the plan's stage twiddles).
+template <typename C, typename Ld, typename St>
+__device__ __forceinline__ void stage_io(const Plan1D<C>& p, int s, const C* stw, int nlines,
+                                         const FastDiv& fnl, bool inv, Ld ld, St st) {
+  const C* tw = stw + p.twoff[s];
+  switch (p.radix[s]) {
+    case 2: stockham_stage_io<2, C>(p.L, p.Ns[s], p.fNs[s], nlines, fnl, tw, inv, ld, st); break;
+    case 3: stockham_stage_io<3, C>(p.L, p.Ns[s], p.fNs[s], nlines, fnl, tw, inv, ld, st); break;
+    case 4: stockham_stage_io<4, C>(p.L, p.Ns[s], p.fNs[s], nlines, fnl, tw, inv, ld, st); break;
+    case 5: stockham_stage_io<5, C>(p.L, p.Ns[s], p.fNs[s], nlines, fnl, tw, inv, ld, st); break;
+    case 7: stockham_stage_io<7, C>(p.L, p.Ns[s], p.fNs[s], nlines, fnl, tw, inv, ld, st); break;
+    case 9: stockham_stage_io<9, C>(p.L, p.Ns[s], p.fNs[s], nlines, fnl, tw, inv, ld, st); break;
+    case 16: stockham_stage_io<16, C>(p.L, p.Ns[s], p.fNs[s], nlines, fnl, tw, inv, ld, st); break;
+    default: stockham_stage_io<8, C>(p.L, p.Ns[s], p.fNs[s], nlines, fnl, tw, inv, ld, st); break;
+  }
+}
+
 // Dispatch a power-of-two tile width (1..16) to a template instantiation.
 #define VC_TILE_DISPATCH(W, F) \
   switch (W) {                 \

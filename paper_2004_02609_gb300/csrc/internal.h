@@ -126,13 +126,18 @@ struct Handle {
   Geom g;
   Panels pan;
   Precond pre;
-  // FFT plans (twiddles owned here)
-  DBuf<double2> twd[3];
-  DBuf<float2> twf[3];
+  // FFT plans; their stage twiddles and the half-voxel phases live in one
+  // device table uploaded with a single copy
+  DBuf<char> plan_tab;
   Plan1D<double2> pd[3];
   Plan1D<float2> pf[3];
-  DBuf<double2> phd[3];           // exp(+i pi k / M) per axis, k in [0, M)
-  DBuf<float2> phf[3];
+  // the same transforms with the radix order reversed: the inverse z
+  // transform of the products starts with the radix the forward one ends
+  // with, so the two meet in registers
+  Plan1D<double2> pdr[3];
+  Plan1D<float2> pfr[3];
+  const double2* phd[3] = {nullptr, nullptr, nullptr};   // exp(+i pi k / M) per axis, k in [0, M)
+  const float2* phf[3] = {nullptr, nullptr, nullptr};
   // Toeplitz tensors (FP64) and spectra
   int tdims[kNumKernels][3];
   DBuf<double> toep[kNumKernels];
@@ -147,6 +152,31 @@ struct Handle {
   bool have_rho = false;
   DBuf<char> solver_ws;
 };
+
+// ---- per-precision views of the handle's plans, phases and spectra
+template <typename T> inline const Plan1D<C_t<T>>& plan_of(const Handle& h, int a);
+template <> inline const Plan1D<float2>& plan_of<float>(const Handle& h, int a) { return h.pf[a]; }
+template <> inline const Plan1D<double2>& plan_of<double>(const Handle& h, int a) { return h.pd[a]; }
+template <typename T> inline const Plan1D<C_t<T>>& plan_rev_of(const Handle& h, int a);
+template <> inline const Plan1D<float2>& plan_rev_of<float>(const Handle& h, int a) { return h.pfr[a]; }
+template <> inline const Plan1D<double2>& plan_rev_of<double>(const Handle& h, int a) { return h.pdr[a]; }
+template <typename T> inline const C_t<T>* phase_of(const Handle& h, int a);
+template <> inline const float2* phase_of<float>(const Handle& h, int a) { return h.phf[a]; }
+template <> inline const double2* phase_of<double>(const Handle& h, int a) { return h.phd[a]; }
+template <typename T> inline const T* spec_of(const Handle& h);
+template <> inline const float* spec_of<float>(const Handle& h) { return h.spec_f.p; }
+template <> inline const double* spec_of<double>(const Handle& h) { return h.spec_d.p; }
+
+// opt a kernel in to `bytes` of dynamic shared memory
+template <typename K> inline int set_smem(K kernel, size_t bytes) {
+  VC_CHECK(bytes <= 227 * 1024, VOXCAP_ERR_UNSUPPORTED, "FFT tile does not fit in shared memory");
+  VC_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  return VOXCAP_OK;
+}
+
+// The z pass of a product (z transforms, spectral multiply-accumulate,
+// inverse z transforms) over B batch items of the y/z-pass buffer, in place.
+template <typename T, bool ADJ> int zmac_launch(const Handle& h, C_t<T>* data, int B, cudaStream_t st);
 
 // ---- module entry points (host side) ----
 int build_fft_plans(Handle& h);

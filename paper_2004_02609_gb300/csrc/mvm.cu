@@ -24,46 +24,6 @@
 
 namespace vc {
 
-__constant__ int c_sig_y[kNumKernels];
-__constant__ int c_sig_z[kNumKernels];
-
-// fold sign of kernel kk along axis a: R(M-k) = sig * R(k)
-static int fold_sign(int kk, int a) {
-  const int te = ker_test(kk), so = ker_src(kk);
-  const bool E = kk >= 6;
-  if (te == so) return (E && a == te) ? -1 : 1;
-  if (a == te) return E ? 1 : -1;
-  if (a == so) return -1;
-  return 1;
-}
-
-static int ensure_sign_tables() {
-  int dev = 0;
-  VC_CUDA(cudaGetDevice(&dev));
-  static bool done[64] = {false};
-  if (dev < 64 && done[dev]) return VOXCAP_OK;
-  int sy[kNumKernels], sz[kNumKernels];
-  for (int kk = 0; kk < kNumKernels; ++kk) { sy[kk] = fold_sign(kk, 1); sz[kk] = fold_sign(kk, 2); }
-  VC_CUDA(cudaMemcpyToSymbol(c_sig_y, sy, sizeof(sy)));
-  VC_CUDA(cudaMemcpyToSymbol(c_sig_z, sz, sizeof(sz)));
-  if (dev < 64) done[dev] = true;
-  return VOXCAP_OK;
-}
-
-// index of the potential block of an unordered orientation pair, and of the
-// field block of an ordered (test, source) pair
-__device__ __forceinline__ int pidx(int a, int b) {
-  if (a == b) return a;
-  int lo = a < b ? a : b, hi = a < b ? b : a;
-  return lo == 0 ? (hi == 1 ? 3 : 4) : 5;
-}
-__device__ __forceinline__ int eidx(int a, int b) {
-  if (a == b) return 6 + a;
-  if (a == 0) return b == 1 ? 9 : 10;
-  if (a == 1) return b == 2 ? 11 : 12;
-  return b == 0 ? 13 : 14;
-}
-
 struct MvmArgs {
   Geom g;
   int nrhs;
@@ -152,6 +112,9 @@ __global__ void k_xfwd(MvmArgs a, const T* __restrict__ xin, C_t<T>* __restrict_
 // in: [B][G][Lz][Lin][H] -> out: [B][G][Lz][Lout][H], transform along the
 // second-fastest axis.  Forward: Lin = Ly (zero-padded to My), Lout = My,
 // phase after.  Inverse: Lin = My, Lout = Ly (truncated), conj phase before.
+// The first stage reads global memory and the last one writes it; shared
+// memory holds the lines between stages (a second buffer only when there
+// are middle stages).
 template <typename T, bool INV, int TX>
 __global__ void k_ypass(Geom g, int G, const C_t<T>* __restrict__ in, C_t<T>* __restrict__ out,
                         int64_t in_bstride, int64_t out_bstride,
@@ -159,9 +122,10 @@ __global__ void k_ypass(Geom g, int G, const C_t<T>* __restrict__ in, C_t<T>* __
   using C = C_t<T>;
   extern __shared__ unsigned char smem_raw[];
   const int M = g.My, H = g.Hx;
+  const int nst = plan.nst;
   C* buf = reinterpret_cast<C*>(smem_raw);
-  C* scr = buf + (size_t)M * TX;
-  C* stw = scr + (size_t)M * TX;
+  C* alt = buf + (size_t)M * TX;
+  C* stw = alt + (nst >= 3 ? (size_t)M * TX : 0);
   load_twiddles(stw, plan);
   const int k0 = blockIdx.x * TX;
   const int z = blockIdx.y;
@@ -170,131 +134,40 @@ __global__ void k_ypass(Geom g, int G, const C_t<T>* __restrict__ in, C_t<T>* __
   const bool phase = (grid % 3) == 1;
   const int Lin = INV ? M : g.Ly;
   const int Lout = INV ? g.Ly : M;
-  const C* src = in + (int64_t)b * in_bstride + ((int64_t)grid * g.Lz + z) * ((int64_t)Lin * H);
-  C* dst = out + (int64_t)b * out_bstride + ((int64_t)grid * g.Lz + z) * ((int64_t)Lout * H);
-  for (int t = threadIdx.x; t < M * TX; t += blockDim.x) {
-    const int c = t % TX, y = t / TX;
-    const int kx = k0 + c;
+  const int ncol = min(TX, H - k0);
+  const C* src = in + (int64_t)b * in_bstride + ((int64_t)grid * g.Lz + z) * ((int64_t)Lin * H) + k0;
+  C* dst = out + (int64_t)b * out_bstride + ((int64_t)grid * g.Lz + z) * ((int64_t)Lout * H) + k0;
+  const FastDiv fTX = make_fastdiv((uint32_t)TX);
+  auto gload = [&](int c, int y) -> C {
     C v = mk<C>((T)0, (T)0);
-    if (kx < H && y < Lin) {
-      v = src[(int64_t)y * H + kx];
+    if (c < ncol && y < Lin) {
+      v = src[(int64_t)y * H + c];
       if (INV && phase) v = cmul(v, cconj(phy[y]));
     }
-    buf[y * TX + c] = v;
-  }
-  __syncthreads();
-  C* res = fft_lines<TX>(buf, scr, TX, plan, stw, INV);
-  for (int t = threadIdx.x; t < Lout * TX; t += blockDim.x) {
-    const int c = t % TX, y = t / TX;
-    const int kx = k0 + c;
-    if (kx >= H) continue;
-    C v = res[y * TX + c];
-    if (!INV && phase) v = cmul(v, phy[y]);
-    dst[(int64_t)y * H + kx] = v;
-  }
-}
-
-// ------------------------------------------------------------------ zmac
-// data: [B][6][Lz][My][H] (in place).  Forward reads grids 0..2, writes 0..5
-// (potential x,y,z then field x,y,z).  Adjoint reads 0..5 (conductor-source
-// x,y,z then dielectric-source x,y,z) and writes 0..2.
-template <typename T, bool ADJ, int TX>
-__global__ void k_zmac(Geom g, C_t<T>* __restrict__ data, const T* __restrict__ spec,
-                       Plan1D<C_t<T>> plan, const C_t<T>* __restrict__ phz) {
-  using C = C_t<T>;
-  extern __shared__ unsigned char smem_raw[];
-  constexpr int GI = ADJ ? 6 : 3;
-  constexpr int GO = ADJ ? 3 : 6;
-  const int M = g.Mz, H = g.Hx;
-  C* bufA = reinterpret_cast<C*>(smem_raw);
-  C* bufB = bufA + (size_t)M * 6 * TX;
-  C* stw = bufB + (size_t)M * 6 * TX;
-  load_twiddles(stw, plan);
-  const int b = blockIdx.x;
-  const int k0 = blockIdx.y * TX;
-  const int ky = blockIdx.z;
-  const int64_t gstride = (int64_t)g.Lz * g.My * H;     // one grid of one batch item
-  C* base = data + (int64_t)b * 6 * gstride + (int64_t)ky * H;
-  constexpr int LI = GI * TX;
-  for (int t = threadIdx.x; t < M * LI; t += blockDim.x) {
-    const int col = t % LI, z = t / LI;
-    const int grid = col / TX, c = col % TX;
-    const int kx = k0 + c;
-    C v = mk<C>((T)0, (T)0);
-    if (kx < H && z < g.Lz) v = base[grid * gstride + (int64_t)z * g.My * H + kx];
-    bufA[z * LI + col] = v;
-  }
-  __syncthreads();
-  C* res = fft_lines<LI>(bufA, bufB, LI, plan, stw, false);
-  C* outb = (res == bufA) ? bufB : bufA;
-  constexpr int LO = GO * TX;
-  const int64_t Otot = (int64_t)H * g.Oy * g.Oz;
-  const bool fy = ky > g.My / 2;
-  const int kyf = fy ? g.My - ky : ky;
-  for (int t = threadIdx.x; t < M * TX; t += blockDim.x) {
-    const int c = t % TX, kz = t / TX;
-    const int kx = k0 + c;
-    C o[GO];
-#pragma unroll
-    for (int q = 0; q < GO; ++q) o[q] = mk<C>((T)0, (T)0);
-    if (kx < H) {
-      const bool fz = kz > M / 2;
-      const int kzf = fz ? M - kz : kz;
-      const int64_t idx = ((int64_t)kzf * g.Oy + kyf) * H + kx;
-      T R[kNumKernels];
-#pragma unroll
-      for (int kk = 0; kk < kNumKernels; ++kk) {
-        T v = spec[kk * Otot + idx];
-        int sg = (fy ? c_sig_y[kk] : 1) * (fz ? c_sig_z[kk] : 1);
-        R[kk] = sg < 0 ? -v : v;
-      }
-      const C ph = phz[kz];
-      C in[GI];
-#pragma unroll
-      for (int q = 0; q < GI; ++q) {
-        in[q] = res[kz * LI + q * TX + c];
-        if (q % 3 == 2) in[q] = cmul(in[q], ph);     // half-voxel shift of z grids
-      }
-      if (!ADJ) {
-#pragma unroll
-        for (int al = 0; al < 3; ++al) {
-          C pa = mk<C>((T)0, (T)0), ea = mk<C>((T)0, (T)0);
-#pragma unroll
-          for (int be = 0; be < 3; ++be) {
-            pa = cadd(pa, cscale(in[be], R[pidx(al, be)]));
-            ea = cadd(ea, cscale(in[be], R[eidx(al, be)]));
-          }
-          o[al] = pa;
-          o[3 + al] = cmul_mi(ea);
-        }
-      } else {
-#pragma unroll
-        for (int be = 0; be < 3; ++be) {
-          C acc = mk<C>((T)0, (T)0), ei = mk<C>((T)0, (T)0);
-#pragma unroll
-          for (int al = 0; al < 3; ++al) {
-            acc = cadd(acc, cscale(in[al], R[pidx(al, be)]));
-            ei = cadd(ei, cscale(in[3 + al], R[eidx(al, be)]));
-          }
-          o[be] = cadd(acc, cmul_pi(ei));
-        }
-      }
-      const C phc = cconj(ph);
-#pragma unroll
-      for (int q = 0; q < GO; ++q)
-        if (q % 3 == 2) o[q] = cmul(o[q], phc);
+    return v;
+  };
+  auto gstore = [&](int c, int y, C v) {
+    if (c < ncol && y < Lout) {
+      if (!INV && phase) v = cmul(v, phy[y]);
+      dst[(int64_t)y * H + c] = v;
     }
-#pragma unroll
-    for (int q = 0; q < GO; ++q) outb[kz * LO + q * TX + c] = o[q];
-  }
+  };
   __syncthreads();
-  C* res2 = fft_lines<LO>(outb, res, LO, plan, stw, true);
-  for (int t = threadIdx.x; t < g.Lz * LO; t += blockDim.x) {
-    const int col = t % LO, z = t / LO;
-    const int grid = col / TX, c = col % TX;
-    const int kx = k0 + c;
-    if (kx < H) base[grid * gstride + (int64_t)z * g.My * H + kx] = res2[z * LO + col];
+  if (nst == 1) {
+    stage_io(plan, 0, stw, TX, fTX, INV, gload, gstore);
+    return;
   }
+  stage_io(plan, 0, stw, TX, fTX, INV, gload, [&](int c, int y, C v) { buf[y * TX + c] = v; });
+  __syncthreads();
+  C* a = buf;
+  C* o = alt;
+  for (int s = 1; s < nst - 1; ++s) {
+    stage_io(plan, s, stw, TX, fTX, INV, [&](int c, int y) { return a[y * TX + c]; },
+             [&](int c, int y, C v) { o[y * TX + c] = v; });
+    __syncthreads();
+    C* t = a; a = o; o = t;
+  }
+  stage_io(plan, nst - 1, stw, TX, fTX, INV, [&](int c, int y) { return a[y * TX + c]; }, gstore);
 }
 
 // ------------------------------------------------------------------ xinv
@@ -393,27 +266,9 @@ template <typename T> static int smem_lines(int L, int cols_per_line, int maxl) 
   return p;
 }
 
-template <typename T> static const Plan1D<C_t<T>>& plan_of(const Handle& h, int a);
-template <> const Plan1D<float2>& plan_of<float>(const Handle& h, int a) { return h.pf[a]; }
-template <> const Plan1D<double2>& plan_of<double>(const Handle& h, int a) { return h.pd[a]; }
-template <typename T> static const C_t<T>* phase_of(const Handle& h, int a);
-template <> const float2* phase_of<float>(const Handle& h, int a) { return h.phf[a].p; }
-template <> const double2* phase_of<double>(const Handle& h, int a) { return h.phd[a].p; }
-template <typename T> static const T* spec_of(const Handle& h);
-template <> const float* spec_of<float>(const Handle& h) { return h.spec_f.p; }
-template <> const double* spec_of<double>(const Handle& h) { return h.spec_d.p; }
-
-template <typename T, typename K>
-static int set_smem(K kernel, size_t bytes) {
-  VC_CHECK(bytes <= 227 * 1024, VOXCAP_ERR_UNSUPPORTED, "FFT tile does not fit in shared memory");
-  VC_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-  return VOXCAP_OK;
-}
-
 template <typename T>
 int mvm(Handle& h, const T* x, T* y, int nrhs, bool adjoint, T* field_out, void* workspace) {
   using C = C_t<T>;
-  VC_TRY(ensure_sign_tables());
   const Geom& g = h.g;
   const int B = h.pan.S * nrhs;
   const int64_t gX = (int64_t)g.Lz * g.Ly * g.Hx;     // one grid, x-pass layout
@@ -444,10 +299,10 @@ int mvm(Handle& h, const T* x, T* y, int nrhs, bool adjoint, T* field_out, void*
     size_t sm = (2 * (size_t)g.Mx * NL + plan_of<T>(h, 0).twn) * sizeof(C);
 #define VC_XFWD(W)                                                                            \
   if (adjoint) {                                                                              \
-    VC_TRY(set_smem<T>(k_xfwd<T, true, W>, sm));                                              \
+    VC_TRY(set_smem(k_xfwd<T, true, W>, sm));                                              \
     k_xfwd<T, true, W><<<grid, TB, sm, st>>>(a, x, bufX, plan_of<T>(h, 0), phase_of<T>(h, 0)); \
   } else {                                                                                    \
-    VC_TRY(set_smem<T>(k_xfwd<T, false, W>, sm));                                             \
+    VC_TRY(set_smem(k_xfwd<T, false, W>, sm));                                             \
     k_xfwd<T, false, W><<<grid, TB, sm, st>>>(a, x, bufX, plan_of<T>(h, 0), phase_of<T>(h, 0)); \
   }
     VC_TILE_DISPATCH(NL, VC_XFWD)
@@ -458,10 +313,10 @@ int mvm(Handle& h, const T* x, T* y, int nrhs, bool adjoint, T* field_out, void*
   // yfwd: bufX [B][GI] -> bufY [B][6] (first GI grids)
   const int TXy = smem_lines<T>(g.My, 1, 16);
   {
-    size_t sm = (2 * (size_t)g.My * TXy + plan_of<T>(h, 1).twn) * sizeof(C);
+    size_t sm = ((plan_of<T>(h, 1).nst >= 3 ? 2 : 1) * (size_t)g.My * TXy + plan_of<T>(h, 1).twn) * sizeof(C);
     dim3 grid((g.Hx + TXy - 1) / TXy, g.Lz, B * GI);
 #define VC_YFWD(W)                                                                          \
-  VC_TRY(set_smem<T>(k_ypass<T, false, W>, sm));                                            \
+  VC_TRY(set_smem(k_ypass<T, false, W>, sm));                                            \
   k_ypass<T, false, W><<<grid, TB, sm, st>>>(g, GI, bufX, bufY, (int64_t)GI * gX, (int64_t)6 * gY, \
                                              plan_of<T>(h, 1), phase_of<T>(h, 1));
     VC_TILE_DISPATCH(TXy, VC_YFWD)
@@ -470,29 +325,14 @@ int mvm(Handle& h, const T* x, T* y, int nrhs, bool adjoint, T* field_out, void*
     VC_CUDA(cudaGetLastError());
   }
   // zmac
-  {
-    const int TXz = smem_lines<T>(g.Mz, 6, 16);
-    size_t sm = (2 * (size_t)g.Mz * 6 * TXz + plan_of<T>(h, 2).twn) * sizeof(C);
-    dim3 grid(B, (g.Hx + TXz - 1) / TXz, g.My);
-#define VC_ZMAC(W)                                                                           \
-  if (adjoint) {                                                                             \
-    VC_TRY(set_smem<T>(k_zmac<T, true, W>, sm));                                             \
-    k_zmac<T, true, W><<<grid, TB, sm, st>>>(g, bufY, spec_of<T>(h), plan_of<T>(h, 2), phase_of<T>(h, 2)); \
-  } else {                                                                                   \
-    VC_TRY(set_smem<T>(k_zmac<T, false, W>, sm));                                            \
-    k_zmac<T, false, W><<<grid, TB, sm, st>>>(g, bufY, spec_of<T>(h), plan_of<T>(h, 2), phase_of<T>(h, 2)); \
-  }
-    VC_TILE_DISPATCH(TXz, VC_ZMAC)
-#undef VC_ZMAC
-    ::vc::note_launch();
-    VC_CUDA(cudaGetLastError());
-  }
+  if (adjoint) VC_TRY((zmac_launch<T, true>(h, bufY, B, st)));
+  else VC_TRY((zmac_launch<T, false>(h, bufY, B, st)));
   // yinv: bufY [B][6] (first GO grids) -> bufX [B][GO]
   {
-    size_t sm = (2 * (size_t)g.My * TXy + plan_of<T>(h, 1).twn) * sizeof(C);
+    size_t sm = ((plan_of<T>(h, 1).nst >= 3 ? 2 : 1) * (size_t)g.My * TXy + plan_of<T>(h, 1).twn) * sizeof(C);
     dim3 grid((g.Hx + TXy - 1) / TXy, g.Lz, B * GO);
 #define VC_YINV(W)                                                                         \
-  VC_TRY(set_smem<T>(k_ypass<T, true, W>, sm));                                            \
+  VC_TRY(set_smem(k_ypass<T, true, W>, sm));                                            \
   k_ypass<T, true, W><<<grid, TB, sm, st>>>(g, GO, bufY, bufX, (int64_t)6 * gY, (int64_t)GO * gX, \
                                             plan_of<T>(h, 1), phase_of<T>(h, 1));
     VC_TILE_DISPATCH(TXy, VC_YINV)
@@ -508,10 +348,10 @@ int mvm(Handle& h, const T* x, T* y, int nrhs, bool adjoint, T* field_out, void*
     size_t sm = (2 * (size_t)g.Mx * NL + plan_of<T>(h, 0).twn) * sizeof(C);
 #define VC_XINV(W)                                                                             \
   if (adjoint) {                                                                               \
-    VC_TRY(set_smem<T>(k_xinv<T, true, W>, sm));                                               \
+    VC_TRY(set_smem(k_xinv<T, true, W>, sm));                                               \
     k_xinv<T, true, W><<<grid, TB, sm, st>>>(a, bufX, x, y, field_out, plan_of<T>(h, 0), phase_of<T>(h, 0)); \
   } else {                                                                                     \
-    VC_TRY(set_smem<T>(k_xinv<T, false, W>, sm));                                              \
+    VC_TRY(set_smem(k_xinv<T, false, W>, sm));                                              \
     k_xinv<T, false, W><<<grid, TB, sm, st>>>(a, bufX, x, y, field_out, plan_of<T>(h, 0), phase_of<T>(h, 0)); \
   }
     VC_TILE_DISPATCH(NL, VC_XINV)
@@ -526,7 +366,6 @@ template int mvm<float>(Handle&, const float*, float*, int, bool, float*, void*)
 template int mvm<double>(Handle&, const double*, double*, int, bool, double*, void*);
 
 int mvm_prepare(Handle& h, int nrhs, size_t complex_bytes) {
-  VC_TRY(ensure_sign_tables());
   return h.ws.alloc(mvm_workspace_bytes(h, nrhs, complex_bytes));
 }
 

@@ -13,7 +13,9 @@
 // spectra (exp(+i pi k_b/M_b) on grid b) and to the results
 // (exp(-i pi k_a/M_a) on grid a).  P^{yx}, P^{zx}, P^{zy} are the same real R
 // as P^{xy}, P^{xz}, P^{yz}: this is Eq. 12 in the shifted frame.
+#include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "internal.h"
@@ -81,38 +83,84 @@ static void fill_tables(std::vector<C>& stw, std::vector<C>& ph, int L, const in
   }
 }
 
+// Host staging of the plan tables: each table starts on a 16-byte boundary.
+struct TableStage {
+  std::vector<char> bytes;
+  template <typename C> size_t put(const std::vector<C>& v) {
+    const size_t off = (bytes.size() + 15) / 16 * 16;
+    bytes.resize(off + std::max<size_t>(v.size(), 1) * sizeof(C));
+    if (!v.empty()) std::memcpy(bytes.data() + off, v.data(), v.size() * sizeof(C));
+    return off;
+  }
+};
+
+// Fill the FP64/FP32 plans of one radix order and stage their twiddles (and
+// the phases, when asked); the offsets into the staged table come back.
+static void make_plan(int L, const int* rad, int nst, TableStage& ts, Plan1D<double2>& pd,
+                      Plan1D<float2>& pf, size_t* off_d, size_t* off_f, size_t* ph_d, size_t* ph_f) {
+  int Ns[kMaxStages], twoff[kMaxStages];
+  std::vector<double2> twd, phd;
+  std::vector<float2> twf, phf;
+  fill_tables(twd, phd, L, rad, nst, Ns, twoff);
+  fill_tables(twf, phf, L, rad, nst, Ns, twoff);
+  *off_d = ts.put(twd);
+  *off_f = ts.put(twf);
+  if (ph_d) {
+    *ph_d = ts.put(phd);
+    *ph_f = ts.put(phf);
+  }
+  pd.L = pf.L = L;
+  pd.nst = pf.nst = nst;
+  pd.twn = pf.twn = (int)twd.size();
+  for (int s = 0; s < nst; ++s) {
+    pd.radix[s] = pf.radix[s] = rad[s];
+    pd.Ns[s] = pf.Ns[s] = Ns[s];
+    pd.fNs[s] = pf.fNs[s] = make_fastdiv((uint32_t)Ns[s]);
+    pd.twoff[s] = pf.twoff[s] = twoff[s];
+  }
+}
+
 int build_fft_plans(Handle& h) {
   Geom& g = h.g;
   int n[3] = {g.nx, g.ny, g.nz};
   int M[3];
+  TableStage ts;
+  size_t off[3][6];
   for (int a = 0; a < 3; ++a) {
     M[a] = pick_length(n[a], h.opts.pad_mode);
-    int rad[kMaxStages], nst = 0, Ns[kMaxStages], twoff[kMaxStages];
+    int rad[kMaxStages], nst = 0;
     VC_CHECK(factor_length(M[a], rad, &nst), VOXCAP_ERR_UNSUPPORTED,
              "FFT length " + std::to_string(M[a]) + " is not 2/3/5/7-smooth (use pad_mode 0)");
-    std::vector<double2> twd, phd;
-    std::vector<float2> twf, phf;
-    fill_tables(twd, phd, M[a], rad, nst, Ns, twoff);
-    fill_tables(twf, phf, M[a], rad, nst, Ns, twoff);
-    const size_t ntw = std::max<size_t>(twd.size(), 1);
-    VC_TRY(h.twd[a].alloc(ntw)); VC_TRY(h.twf[a].alloc(ntw));
-    VC_TRY(h.phd[a].alloc(M[a])); VC_TRY(h.phf[a].alloc(M[a]));
-    if (!twd.empty()) {
-      VC_CUDA(cudaMemcpy(h.twd[a].p, twd.data(), sizeof(double2) * twd.size(), cudaMemcpyHostToDevice));
-      VC_CUDA(cudaMemcpy(h.twf[a].p, twf.data(), sizeof(float2) * twf.size(), cudaMemcpyHostToDevice));
+    if (a == 2) {
+      // the z pass keeps its last forward radix in registers: the largest
+      // radix <= 9 goes last, and a last 16 (too many registers per line
+      // and grid) is split into 4 x 4
+      int best = -1;
+      for (int s = 0; s < nst; ++s)
+        if (rad[s] <= 9 && (best < 0 || rad[s] > rad[best])) best = s;
+      if (best < 0) best = 0;
+      std::swap(rad[best], rad[nst - 1]);
+      if (rad[nst - 1] == 16) {
+        rad[nst - 1] = 4;
+        rad[nst++] = 4;
+      }
     }
-    VC_CUDA(cudaMemcpy(h.phd[a].p, phd.data(), sizeof(double2) * M[a], cudaMemcpyHostToDevice));
-    VC_CUDA(cudaMemcpy(h.phf[a].p, phf.data(), sizeof(float2) * M[a], cudaMemcpyHostToDevice));
-    for (Plan1D<double2>* pd : {&h.pd[a]}) {
-      pd->L = M[a]; pd->nst = nst; pd->twn = (int)twd.size(); pd->stw = h.twd[a].p;
-    }
-    h.pf[a].L = M[a]; h.pf[a].nst = nst; h.pf[a].twn = (int)twf.size(); h.pf[a].stw = h.twf[a].p;
-    for (int s = 0; s < nst; ++s) {
-      h.pd[a].radix[s] = h.pf[a].radix[s] = rad[s];
-      h.pd[a].Ns[s] = h.pf[a].Ns[s] = Ns[s];
-      h.pd[a].fNs[s] = h.pf[a].fNs[s] = make_fastdiv((uint32_t)Ns[s]);
-      h.pd[a].twoff[s] = h.pf[a].twoff[s] = twoff[s];
-    }
+    make_plan(M[a], rad, nst, ts, h.pd[a], h.pf[a], &off[a][0], &off[a][1], &off[a][2], &off[a][3]);
+    int rev[kMaxStages];
+    for (int s = 0; s < nst; ++s) rev[s] = rad[nst - 1 - s];
+    make_plan(M[a], rev, nst, ts, h.pdr[a], h.pfr[a], &off[a][4], &off[a][5], nullptr, nullptr);
+  }
+  VC_TRY(h.plan_tab.alloc(ts.bytes.size()));
+  // from pageable memory: returns once the bytes are staged, so `ts` may go
+  VC_CUDA(cudaMemcpyAsync(h.plan_tab.p, ts.bytes.data(), ts.bytes.size(), cudaMemcpyHostToDevice, h.stream));
+  char* base = h.plan_tab.p;
+  for (int a = 0; a < 3; ++a) {
+    h.pd[a].stw = reinterpret_cast<const double2*>(base + off[a][0]);
+    h.pf[a].stw = reinterpret_cast<const float2*>(base + off[a][1]);
+    h.phd[a] = reinterpret_cast<const double2*>(base + off[a][2]);
+    h.phf[a] = reinterpret_cast<const float2*>(base + off[a][3]);
+    h.pdr[a].stw = reinterpret_cast<const double2*>(base + off[a][4]);
+    h.pfr[a].stw = reinterpret_cast<const float2*>(base + off[a][5]);
   }
   g.Mx = M[0]; g.My = M[1]; g.Mz = M[2];
   g.Hx = g.Mx / 2 + 1;
@@ -333,7 +381,7 @@ int build_spectra(Handle& h) {
       VC_CUDA(cudaGetLastError());
     }
     k_extract<<<(unsigned)((Otot + TB - 1) / TB), TB, 0, h.stream>>>(
-        spec.p, g, kk, kk >= 6, ker_test(kk), ker_src(kk), h.phd[0].p, h.phd[1].p, h.phd[2].p,
+        spec.p, g, kk, kk >= 6, ker_test(kk), ker_src(kk), h.phd[0], h.phd[1], h.phd[2],
         scale, h.spec_d.p + (size_t)kk * Otot, h.spec_f.p + (size_t)kk * Otot); ::vc::note_launch();
     VC_CUDA(cudaGetLastError());
   }
