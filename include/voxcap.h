@@ -63,6 +63,12 @@ extern "C" {
 #define VOXCAP_FP64 0            /* plain FP64 GMRES with FP64 FFT products */
 #define VOXCAP_FP32_REFINE 1     /* FP32 GMRES / FP32 FFT products inside FP64 iterative refinement */
 
+/* precision of the generated Toeplitz entries (voxcap_opts.entries) */
+#define VOXCAP_ENTRIES_AUTO 0    /* FP32 far field under VOXCAP_FP32_REFINE, FP64 under VOXCAP_FP64 */
+#define VOXCAP_ENTRIES_FP64 1    /* every entry in FP64 (near-field closed forms, far-field quadrature) */
+#define VOXCAP_ENTRIES_FAR32 2   /* near-field closed forms in FP64, far-field quadrature sums in FP32
+                                    (entries to about 1e-7 relative, the FP32 products' accuracy) */
+
 /* dtypes of voxcap_matvec */
 #define VOXCAP_F32 0
 #define VOXCAP_F64 1
@@ -107,6 +113,7 @@ typedef struct voxcap_opts {
                              the FFT engine's cost model (default);
                           1: the paper's M = 2(N+1) (must be 2/3/5/7-smooth);
                           2: the smallest even 2/3/5/7-smooth length */
+  int entries;         /* VOXCAP_ENTRIES_* (default AUTO): precision of the generated entries */
   const voxcap_tucker* tucker; /* NULL: generate the Toeplitz tensors in FP64 (Eqs. 5-6);
                           else restore them from these Tucker factors on the
                           tensor cores (Sec. II.C), cropped to the grid */

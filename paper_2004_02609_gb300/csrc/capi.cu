@@ -31,6 +31,7 @@ void voxcap_default_opts(voxcap_opts* o) {
   o->nv[0] = o->nv[1] = o->nv[2] = 10;
   o->precond = VOXCAP_PRECOND_BDD;
   o->pad_mode = 0;
+  o->entries = VOXCAP_ENTRIES_AUTO;
   o->tucker = nullptr;
 }
 
@@ -63,6 +64,8 @@ static int setup_impl(const int32_t* labels, int nx, int ny, int nz, int n_struc
   if (opts) h.opts = *opts; else voxcap_default_opts(&h.opts);
   if (h.opts.restart < 1) h.opts.restart = 35;
   if (h.opts.max_iters < 1) h.opts.max_iters = 2000;
+  VC_CHECK(h.opts.entries >= VOXCAP_ENTRIES_AUTO && h.opts.entries <= VOXCAP_ENTRIES_FAR32, VOXCAP_ERR_ARG,
+           "entries must be one of VOXCAP_ENTRIES_*");
   h.dv = voxel_size_m;
   h.nlab = n_labels;
   h.cid.assign(conductor_id, conductor_id + n_labels);

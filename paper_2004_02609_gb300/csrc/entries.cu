@@ -24,6 +24,12 @@ namespace vc {
 constexpr int kMaxGL = 10;
 __constant__ double c_glx[kMaxGL + 1][kMaxGL];
 __constant__ double c_glw[kMaxGL + 1][kMaxGL];
+// FP32 forms for the far field: half-nodes x/2, half-weights w/2, the
+// triangle-rule abscissae (1+x)/2 and weights (w/2)(1 - (1+x)/2)
+__constant__ float c_fx[kMaxGL + 1][kMaxGL];
+__constant__ float c_fw[kMaxGL + 1][kMaxGL];
+__constant__ float c_fp[kMaxGL + 1][kMaxGL];
+__constant__ float c_fq[kMaxGL + 1][kMaxGL];
 
 // Gauss-Legendre nodes / weights on [-1,1] by Newton iteration on P_n.
 static void gauss_legendre(int n, double* x, double* w) {
@@ -64,6 +70,20 @@ static int ensure_gl_tables() {
   for (int n = 1; n <= kMaxGL; ++n) gauss_legendre(n, hx[n], hw[n]);
   VC_CUDA(cudaMemcpyToSymbol(c_glx, hx, sizeof(hx)));
   VC_CUDA(cudaMemcpyToSymbol(c_glw, hw, sizeof(hw)));
+  float fx[kMaxGL + 1][kMaxGL] = {}, fw[kMaxGL + 1][kMaxGL] = {};
+  float fp[kMaxGL + 1][kMaxGL] = {}, fq[kMaxGL + 1][kMaxGL] = {};
+  for (int n = 1; n <= kMaxGL; ++n)
+    for (int i = 0; i < n; ++i) {
+      const double pp = 0.5 * (1.0 + hx[n][i]);
+      fx[n][i] = (float)(0.5 * hx[n][i]);
+      fw[n][i] = (float)(0.5 * hw[n][i]);
+      fp[n][i] = (float)pp;
+      fq[n][i] = (float)(0.5 * hw[n][i] * (1.0 - pp));
+    }
+  VC_CUDA(cudaMemcpyToSymbol(c_fx, fx, sizeof(fx)));
+  VC_CUDA(cudaMemcpyToSymbol(c_fw, fw, sizeof(fw)));
+  VC_CUDA(cudaMemcpyToSymbol(c_fp, fp, sizeof(fp)));
+  VC_CUDA(cudaMemcpyToSymbol(c_fq, fq, sizeof(fq)));
   if (dev < 64) done[dev] = true;
   return VOXCAP_OK;
 }
@@ -176,9 +196,83 @@ __device__ int gl_order_ort(double gap) {
   return 3;
 }
 
+// ---- far field with FP32 sums ----
+// The same rules with the inner sums in FP32 and the outer accumulation in
+// FP64: entries to about 1e-7 relative, the accuracy of the FP32 products
+// they feed.  Used when the set-up keeps FP64 for the near field only.
+__device__ __forceinline__ float sqrt_approx(float x) { return x * rsqrtf(x); }
+
+__device__ void par_pe_far32(double h, double s, double t, int n, double* P, double* E) {
+  const float hf = (float)h, h2 = hf * hf;
+  const float sf = (float)s, tf = (float)t;
+  double ap = 0.0, ae = 0.0;
+  for (int sp = -1; sp <= 1; sp += 2)
+    for (int i = 0; i < n; ++i) {
+      const float X = sf + (float)sp * c_fp[n][i];
+      const float X2h = X * X + h2;
+      float qp = 0.0f, qe = 0.0f;
+      for (int sq = -1; sq <= 1; sq += 2)
+        for (int j = 0; j < n; ++j) {
+          const float Y = tf + (float)sq * c_fp[n][j];
+          const float ir = rsqrtf(X2h + Y * Y);
+          const float wq = c_fq[n][j];
+          qp += wq * ir;
+          qe += wq * ir * ir * ir;
+        }
+      ap += (double)c_fq[n][i] * (double)qp;
+      ae += (double)c_fq[n][i] * (double)qe;
+    }
+  *P = ap * kInv4Pi;
+  *E = -h * ae * kInv4Pi;
+}
+
+__device__ void ort_pe_far32(double a, double b, double c, int n, double* P, double* Ea, double* Eb) {
+  const int ne = n + 2;
+  const float af = (float)a, bf = (float)b, cf = (float)c;
+  const float ap0 = af + 0.5f, am0 = af - 0.5f, bp0 = bf + 0.5f, bm0 = bf - 0.5f;
+  double ap = 0.0, aa = 0.0, ab = 0.0;
+  for (int sw = -1; sw <= 1; sw += 2) {
+    for (int k = 0; k < n; ++k) {
+      const float Z = cf + (float)sw * c_fp[n][k];
+      const float Z2 = Z * Z;
+      float sj = 0.0f;
+      for (int j = 0; j < n; ++j) {
+        const float q = bf + c_fx[n][j];
+        const float bq = q * q + Z2;
+        float si = 0.0f;
+        for (int i = 0; i < n; ++i) {
+          const float pi = af + c_fx[n][i];
+          si += c_fw[n][i] * rsqrtf(pi * pi + bq);
+        }
+        sj += c_fw[n][j] * si;
+      }
+      ap += (double)c_fq[n][k] * (double)sj;
+    }
+    for (int k = 0; k < ne; ++k) {
+      const float Z = cf + (float)sw * c_fp[ne][k];
+      const float Z2 = Z * Z;
+      float sa = 0.0f, sb = 0.0f;
+      for (int j = 0; j < ne; ++j) {
+        const float u = c_fx[ne][j], wu = c_fw[ne][j];
+        const float q = bf + u, bq = q * q + Z2;
+        const float ra1 = sqrt_approx(ap0 * ap0 + bq), ra0 = sqrt_approx(am0 * am0 + bq);
+        sa += wu * __fdividef(-2.0f * af, ra0 * ra1 * (ra0 + ra1));
+        const float p = af + u, bp = p * p + Z2;
+        const float rb1 = sqrt_approx(bp0 * bp0 + bp), rb0 = sqrt_approx(bm0 * bm0 + bp);
+        sb += wu * __fdividef(-2.0f * bf, rb0 * rb1 * (rb0 + rb1));
+      }
+      aa += (double)c_fq[ne][k] * (double)sa;
+      ab += (double)c_fq[ne][k] * (double)sb;
+    }
+  }
+  *P = ap * kInv4Pi;
+  *Ea = aa * kInv4Pi;
+  *Eb = ab * kInv4Pi;
+}
+
 // ---- P and E together at one evaluation point ----
 // parallel: P = Ppar(h,s,t), E = dPpar/dh
-__device__ void par_pe(double h, double s, double t, double* P, double* E) {
+__device__ void par_pe(double h, double s, double t, double* P, double* E, bool far32 = false) {
   const double gap = fmax(h, fmax(s - 1.0, t - 1.0));
   if (gap <= 1.0) {
     double ap = 0.0, ae = 0.0;
@@ -194,6 +288,10 @@ __device__ void par_pe(double h, double s, double t, double* P, double* E) {
     return;
   }
   const int n = gl_order_par(gap);
+  if (far32) {
+    par_pe_far32(h, s, t, n, P, E);
+    return;
+  }
   double ap = 0.0, ae = 0.0;
   for (int sp = -1; sp <= 1; sp += 2)
     for (int i = 0; i < n; ++i) {
@@ -218,7 +316,8 @@ __device__ void par_pe(double h, double s, double t, double* P, double* E) {
 }
 
 // orthogonal: P = Port(a,b,c), Ea = dPort/da, Eb = dPort/db
-__device__ void ort_pe(double a, double b, double c, double* P, double* Ea, double* Eb) {
+__device__ void ort_pe(double a, double b, double c, double* P, double* Ea, double* Eb,
+                       bool far32 = false) {
   const double gap = fmax(a - 0.5, fmax(b - 0.5, c - 1.0));
   if (gap <= 1.0) {
     *P = ort_cf(false, a, b, c);
@@ -230,6 +329,10 @@ __device__ void ort_pe(double a, double b, double c, double* P, double* Ea, doub
   // they take two more orders, and 1/r1 - 1/r0 is formed without cancellation
   // as ((a-1/2)^2 - (a+1/2)^2) / (r0 r1 (r0 + r1)) = -2a / (r0 r1 (r0 + r1)).
   const int n = gl_order_ort(gap);
+  if (far32) {
+    ort_pe_far32(a, b, c, n, P, Ea, Eb);
+    return;
+  }
   const int ne = n + 2;
   double ap = 0.0, aa = 0.0, ab = 0.0;
   for (int sw = -1; sw <= 1; sw += 2) {
@@ -273,6 +376,7 @@ __device__ void ort_pe(double a, double b, double c, double* P, double* Ea, doub
 
 struct ToepLaunch {
   double* out[kNumKernels];
+  int far32;              // far field with FP32 sums
   int d[6][3];            // extents of the 6 evaluation groups
   int64_t start[7];
 };
@@ -293,14 +397,14 @@ __global__ void k_toeplitz(ToepLaunch L) {
     const int al = gi;
     const int a1 = al == 0 ? 1 : 0, a2 = al == 2 ? 1 : 2;
     double P, E;
-    par_pe((double)e[al], (double)e[a1], (double)e[a2], &P, &E);
+    par_pe((double)e[al], (double)e[a1], (double)e[a2], &P, &E, L.far32 != 0);
     L.out[al][q] = P;
     L.out[6 + al][q] = E;
   } else {
     const int pair = gi - 3;
     const int al = pair == 2 ? 1 : 0, be = pair == 0 ? 1 : 2, ga = 3 - al - be;
     double P, Ea, Eb;
-    ort_pe(e[al] + 0.5, e[be] + 0.5, (double)e[ga], &P, &Ea, &Eb);
+    ort_pe(e[al] + 0.5, e[be] + 0.5, (double)e[ga], &P, &Ea, &Eb, L.far32 != 0);
     L.out[3 + pair][q] = P;
     L.out[9 + pair][q] = Ea;
     L.out[12 + pair][q] = Eb;
@@ -330,6 +434,8 @@ int build_toeplitz(Handle& h) {
     for (int a = 0; a < 3; ++a) L.d[gi][a] = d[a];
     L.start[gi + 1] = L.start[gi] + (int64_t)d[0] * d[1] * d[2];
   }
+  L.far32 = h.opts.entries == VOXCAP_ENTRIES_FAR32 ||
+            (h.opts.entries == VOXCAP_ENTRIES_AUTO && h.opts.precision == VOXCAP_FP32_REFINE);
   const int TB = 128;
   const int64_t tot = L.start[6];
   k_toeplitz<<<(unsigned)((tot + TB - 1) / TB), TB, 0, h.stream>>>(L); ::vc::note_launch();

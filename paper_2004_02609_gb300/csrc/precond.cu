@@ -12,6 +12,7 @@
 // identical blocks, so only one inverse per distinct pattern is stored
 // (Sec. II.D point (ii)).  BD uses all panels of a box (dielectric rows with
 // E' + I'), DIAG uses 1/A_kk and NONE the identity.
+#include <algorithm>
 #include <vector>
 
 #include "internal.h"
@@ -250,13 +251,13 @@ __device__ __forceinline__ void face_coords(const int* n, int o, int f, int* c) 
 
 // assemble [A_B | I] (n x 2n, row-major) for one unique block
 __global__ void k_assemble(ToepTabs tt, const int32_t* urep, const int32_t* offs, const int32_t* idx,
-                           const int64_t* uoff, const int8_t* orient, const int32_t* face,
+                           const int64_t* aoff, const int8_t* orient, const int32_t* face,
                            const int8_t* kind, const double* idiag, double* aug) {
   const int u = blockIdx.x;
   const int gb = urep[u];
   const int q0 = offs[gb];
   const int n = offs[gb + 1] - q0;
-  double* Mx = aug + 2 * uoff[u];
+  double* Mx = aug + aoff[u];
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
     const int i = t / n, j = t % n;
     const int pk = idx[q0 + i], pl = idx[q0 + j];
@@ -268,6 +269,113 @@ __global__ void k_assemble(ToepTabs tt, const int32_t* urep, const int32_t* offs
     if (E && i == j) v += idiag[pk];
     Mx[(int64_t)i * 2 * n + j] = v;
     Mx[(int64_t)i * 2 * n + n + j] = (i == j) ? 1.0 : 0.0;
+  }
+}
+
+// Inverse of one unique block held whole in shared memory (FP32; the
+// preconditioner only steers GMRES, the solution's accuracy comes from the
+// residuals).  In-place Gauss-Jordan with pivot bookkeeping: step k takes
+// as pivot the unused row p_k with the largest |S[p][k]|, scales that row and
+// eliminates column k from every other row; column k, now a unit vector,
+// stores column p_k of the inverse-to-be.  After n steps
+// A^-1[k][j] = S[p_k][q_j] with q the inverse permutation of p.
+constexpr int kGJSmemMax = 224;
+
+__global__ void __launch_bounds__(1024) k_block_inverse(ToepTabs tt, const int32_t* __restrict__ urep,
+                                                        const int32_t* __restrict__ offs,
+                                                        const int32_t* __restrict__ idx,
+                                                        const int64_t* __restrict__ uoff,
+                                                        const int8_t* __restrict__ orient,
+                                                        const int32_t* __restrict__ face,
+                                                        const int8_t* __restrict__ kind,
+                                                        const double* __restrict__ idiag,
+                                                        double* __restrict__ inv_d, float* __restrict__ inv_f,
+                                                        int* __restrict__ status) {
+  extern __shared__ float S[];                       // n rows of stride ld (odd)
+  __shared__ float colb[2][kGJSmemMax], rowb[2][kGJSmemMax];
+  __shared__ int perm[kGJSmemMax], qinv[kGJSmemMax];
+  __shared__ unsigned char used[kGJSmemMax];
+  __shared__ int piv_row[2];
+  __shared__ float piv_inv[2];
+  __shared__ int fail;
+  const int u = blockIdx.x;
+  const int gb = urep[u];
+  const int q0 = offs[gb];
+  const int n = offs[gb + 1] - q0;
+  if (n > kGJSmemMax || n == 0) return;              // larger blocks take the multi-CTA path
+  const int ld = n | 1;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  for (int t = tid; t < n * n; t += nt) {
+    const int i = t / n, j = t - (t / n) * n;
+    const int pk = idx[q0 + i], pl = idx[q0 + j];
+    int ck[3], cl[3];
+    face_coords(tt.n, orient[pk], face[pk], ck);
+    face_coords(tt.n, orient[pl], face[pl], cl);
+    const bool E = kind[pk] == 1;
+    double v = a_entry(tt, E, orient[pk], ck, orient[pl], cl);
+    if (E && i == j) v += idiag[pk];
+    S[i * ld + j] = (float)v;
+  }
+  for (int i = tid; i < n; i += nt) used[i] = 0;
+  if (tid == 0) fail = 0;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    const int b = k & 1;
+    if (wid == 0) {                                  // pivot search over the unused rows
+      float best = -1.0f;
+      int bi = n;
+      for (int i = lane; i < n; i += 32) {
+        const float v = S[i * ld + k];
+        colb[b][i] = v;
+        if (!used[i] && fabsf(v) > best) { best = fabsf(v); bi = i; }
+      }
+      for (int d = 16; d > 0; d >>= 1) {
+        const float ob = __shfl_down_sync(0xffffffffu, best, d);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, d);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) {
+        if (!(best > 0.0f) || bi >= n) {
+          fail = 1;
+          bi = 0;
+          best = 1.0f;
+        }
+        piv_row[b] = bi;
+        piv_inv[b] = 1.0f / colb[b][bi];
+        used[bi] = 1;
+        perm[k] = bi;
+      }
+    }
+    __syncthreads();
+    if (fail) break;                                 // uniform: read after the barrier
+    const int p = piv_row[b];
+    const float ip = piv_inv[b];
+    for (int j = tid; j < n; j += nt) rowb[b][j] = (j == k ? 1.0f : S[p * ld + j]) * ip;
+    __syncthreads();
+    for (int i = wid; i < n; i += nw) {
+      float* row = S + i * ld;
+      if (i == p) {
+        for (int j = lane; j < n; j += 32) row[j] = rowb[b][j];
+      } else {
+        const float f = colb[b][i];
+        for (int j = lane; j < n; j += 32) row[j] = (j == k ? 0.0f : row[j]) - f * rowb[b][j];
+      }
+    }
+    __syncthreads();
+  }
+  if (fail) {
+    if (tid == 0) atomicExch(status, 1);
+    return;
+  }
+  for (int k = tid; k < n; k += nt) qinv[perm[k]] = k;
+  __syncthreads();
+  const int64_t o = uoff[u];
+  for (int t = tid; t < n * n; t += nt) {
+    const int k = t / n, j = t - (t / n) * n;
+    const float v = S[perm[k] * ld + qinv[j]];
+    inv_f[o + t] = v;
+    inv_d[o + t] = (double)v;
   }
 }
 
@@ -284,7 +392,7 @@ __global__ void k_assemble(ToepTabs tt, const int32_t* urep, const int32_t* offs
 constexpr int kGJCols = 16;
 
 __global__ void k_gj_step(int c, const int32_t* __restrict__ urep, const int32_t* __restrict__ offs,
-                          const int64_t* __restrict__ uoff, const int64_t* __restrict__ poff,
+                          const int64_t* __restrict__ aoff, const int64_t* __restrict__ poff,
                           double* __restrict__ aug, const double* __restrict__ pin,
                           double* __restrict__ pout, int* __restrict__ status) {
   extern __shared__ double gsm[];
@@ -296,7 +404,7 @@ __global__ void k_gj_step(int c, const int32_t* __restrict__ urep, const int32_t
   const int j0 = blockIdx.x * kGJCols;
   if (j0 >= w) return;
   const int j1 = min(w, j0 + kGJCols);
-  double* Mx = aug + 2 * uoff[u];
+  double* Mx = aug + aoff[u];
   double* mult = gsm;                 // [n]
   double* prow = gsm + n;             // [kGJCols]
   double* crow = prow + kGJCols;      // [kGJCols]
@@ -350,12 +458,12 @@ __global__ void k_gj_step(int c, const int32_t* __restrict__ urep, const int32_t
     for (int r = threadIdx.x; r < n; r += blockDim.x) pout[poff[u] + r] = Mx[(int64_t)r * w + nc];
 }
 
-__global__ void k_extract_inv(const int32_t* urep, const int32_t* offs, const int64_t* uoff,
-                              const double* aug, double* inv_d, float* inv_f) {
+__global__ void k_extract_inv(const int32_t* urep, const int32_t* offs, const int64_t* aoff,
+                              const int64_t* uoff, const double* aug, double* inv_d, float* inv_f) {
   const int u = blockIdx.x;
   const int gb = urep[u];
   const int n = offs[gb + 1] - offs[gb];
-  const double* Mx = aug + 2 * uoff[u];
+  const double* Mx = aug + aoff[u];
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
     const int i = t / n, j = t % n;
     double v = Mx[(int64_t)i * 2 * n + n + j];
@@ -365,9 +473,10 @@ __global__ void k_extract_inv(const int32_t* urep, const int32_t* offs, const in
 }
 
 __global__ void k_diag_scale(int64_t N, int mode, const int8_t* kind, const double* idiag,
-                             double pself, const int32_t* inblk, double* dd, float* df) {
+                             const double* pself_p, const int32_t* inblk, double* dd, float* df) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= N) return;
+  const double pself = *pself_p;
   double v;
   if (mode == VOXCAP_PRECOND_NONE) v = 1.0;
   else if (mode == VOXCAP_PRECOND_DIAG) v = kind[p] == 0 ? 1.0 / pself : 1.0 / idiag[p];
@@ -391,9 +500,7 @@ int build_precond(Handle& h) {
   const int S = h.pan.S;
   VC_TRY(P.dscale_d.alloc((size_t)std::max<int64_t>(N, 1)));
   VC_TRY(P.dscale_f.alloc((size_t)std::max<int64_t>(N, 1)));
-  // self term P'_kk (identical for every orientation)
-  double pself = 0.0;
-  VC_CUDA(cudaMemcpy(&pself, h.toep[0].p, sizeof(double), cudaMemcpyDeviceToHost));
+  const double* pself = h.toep[0].p;      // self term P'_kk (identical for every orientation)
   const int TB = 256;
   P.nblocks = 0;
   P.nunique = 0;
@@ -402,7 +509,6 @@ int build_precond(Handle& h) {
     k_diag_scale<<<(unsigned)((N + TB - 1) / TB), TB, 0, h.stream>>>(
         N, P.kind, h.pan.kind.p, h.pan.idiag.p, pself, nullptr, P.dscale_d.p, P.dscale_f.p); ::vc::note_launch();
     VC_CUDA(cudaGetLastError());
-    VC_CUDA(cudaStreamSynchronize(h.stream));
     return VOXCAP_OK;
   }
   BoxGeom bg;
@@ -417,106 +523,133 @@ int build_precond(Handle& h) {
   const int64_t nboxes = bg.nbox * S;
   P.nboxes = nboxes;
   P.nblocks = nboxes;
+  // box -> panels (every panel lies in exactly one box, so N bounds the total)
   VC_TRY(P.blk_off.alloc((size_t)nboxes + 1));
   DBuf<int32_t> tmp;
   VC_TRY(tmp.alloc((size_t)scan_tmp_elems(nboxes + 1) + 8));
   VC_CUDA(cudaMemsetAsync(P.blk_off.p, 0, sizeof(int32_t) * (nboxes + 1), h.stream));
   k_box_count<<<(unsigned)nboxes, TB, 0, h.stream>>>(bg, h.pan.fmap.p, h.pan.kind.p, P.kind, P.blk_off.p); ::vc::note_launch();
   VC_CUDA(cudaGetLastError());
-  // counts -> offsets (scan over nboxes+1 so that blk_off[nboxes] = total)
-  std::vector<int32_t> cnt_h(nboxes);
-  VC_CUDA(cudaMemcpyAsync(cnt_h.data(), P.blk_off.p, sizeof(int32_t) * nboxes, cudaMemcpyDeviceToHost, h.stream));
-  int64_t total = 0;
-  VC_TRY(exclusive_scan_i32(P.blk_off.p, nboxes + 1, tmp.p, &total, h.stream));
-  for (int64_t b = 0; b < nboxes; ++b) P.max_n = std::max(P.max_n, (int)cnt_h[b]);
-  VC_TRY(P.blk_idx.alloc((size_t)std::max<int64_t>(total, 1)));
+  VC_TRY(exclusive_scan_i32(P.blk_off.p, nboxes + 1, tmp.p, nullptr, h.stream));
+  VC_TRY(P.blk_idx.alloc((size_t)std::max<int64_t>(N, 1)));
   k_box_fill<<<(unsigned)nboxes, TB, 0, h.stream>>>(bg, h.pan.fmap.p, h.pan.kind.p, P.kind, P.blk_off.p,
                                                    P.blk_idx.p); ::vc::note_launch();
   VC_CUDA(cudaGetLastError());
-  // dedup
+  // dedup: representatives, their flags (kept) and unique ids (scan of a copy)
   DBuf<uint64_t> hash;
-  DBuf<int32_t> rep, isrep;
+  DBuf<int32_t> rep, meta;                 // meta = [blk_off (nboxes + 1) | is_rep (nboxes)]
+  DBuf<int32_t> rep_scan;
   VC_TRY(hash.alloc((size_t)nboxes));
   VC_TRY(rep.alloc((size_t)nboxes));
-  VC_TRY(isrep.alloc((size_t)nboxes + 1));
-  VC_CUDA(cudaMemsetAsync(isrep.p, 0, sizeof(int32_t) * (nboxes + 1), h.stream));
+  VC_TRY(meta.alloc((size_t)2 * nboxes + 1));
+  VC_TRY(rep_scan.alloc((size_t)nboxes + 1));
+  int32_t* isrep = meta.p + nboxes + 1;
   unsigned nbk = (unsigned)((nboxes + TB - 1) / TB);
   k_box_hash<<<nbk, TB, 0, h.stream>>>(bg, nboxes, P.blk_off.p, P.blk_idx.p, h.pan.orient.p,
                                        h.pan.face.p, h.pan.kind.p, h.pan.idiag.p, P.kind, hash.p); ::vc::note_launch();
   k_box_rep<<<nbk, TB, 0, h.stream>>>(bg, nboxes, P.blk_off.p, P.blk_idx.p, h.pan.orient.p,
                                       h.pan.face.p, h.pan.kind.p, h.pan.idiag.p, P.kind, hash.p,
-                                      rep.p, isrep.p); ::vc::note_launch();
+                                      rep.p, isrep); ::vc::note_launch();
   VC_CUDA(cudaGetLastError());
-  // unique ids: scan of is_rep; copy representatives to the host to size the storage
-  std::vector<int32_t> isrep_h(nboxes);
-  VC_CUDA(cudaMemcpyAsync(isrep_h.data(), isrep.p, sizeof(int32_t) * nboxes, cudaMemcpyDeviceToHost, h.stream));
-  int64_t nuniq = 0;
-  VC_TRY(exclusive_scan_i32(isrep.p, nboxes + 1, tmp.p, &nuniq, h.stream));
+  VC_CUDA(cudaMemcpyAsync(rep_scan.p, isrep, sizeof(int32_t) * nboxes, cudaMemcpyDeviceToDevice, h.stream));
+  VC_CUDA(cudaMemsetAsync(rep_scan.p + nboxes, 0, sizeof(int32_t), h.stream));
+  VC_TRY(exclusive_scan_i32(rep_scan.p, nboxes + 1, tmp.p, nullptr, h.stream));
   VC_TRY(P.blk_uid.alloc((size_t)nboxes));
-  k_box_uid<<<nbk, TB, 0, h.stream>>>(nboxes, rep.p, isrep.p, P.blk_off.p, P.blk_uid.p); ::vc::note_launch();
+  k_box_uid<<<nbk, TB, 0, h.stream>>>(nboxes, rep.p, rep_scan.p, P.blk_off.p, P.blk_uid.p); ::vc::note_launch();
+  VC_CUDA(cudaMemcpyAsync(meta.p, P.blk_off.p, sizeof(int32_t) * (nboxes + 1), cudaMemcpyDeviceToDevice,
+                          h.stream));
   VC_CUDA(cudaGetLastError());
-  P.nunique = nuniq;
-  std::vector<int32_t> urep_h;
-  std::vector<int64_t> uoff_h(1, 0);
-  for (int64_t b = 0; b < nboxes; ++b)
-    if (isrep_h[b]) {
-      urep_h.push_back((int32_t)b);
-      uoff_h.push_back(uoff_h.back() + (int64_t)cnt_h[b] * cnt_h[b]);
+  // one read-back sizes the inverse storage (a pageable copy waits for the work above)
+  std::vector<int32_t> meta_h((size_t)2 * nboxes + 1);
+  VC_CUDA(cudaMemcpyAsync(meta_h.data(), meta.p, sizeof(int32_t) * meta_h.size(), cudaMemcpyDeviceToHost,
+                          h.stream));
+  VC_CUDA(cudaStreamSynchronize(h.stream));
+  const int32_t* off_h = meta_h.data();
+  const int32_t* isrep_h = meta_h.data() + nboxes + 1;
+  const int64_t total = off_h[nboxes];
+  std::vector<int32_t> urep_h, urepL_h;
+  std::vector<int64_t> uoff_h(1, 0), uoffL_h, aoffL_h(1, 0);
+  int max_small = 0, max_large = 0;
+  for (int64_t b = 0; b < nboxes; ++b) {
+    const int n = off_h[b + 1] - off_h[b];
+    P.max_n = std::max(P.max_n, n);
+    if (!isrep_h[b]) continue;
+    if (n <= kGJSmemMax) {
+      max_small = std::max(max_small, n);
+    } else {
+      max_large = std::max(max_large, n);
+      urepL_h.push_back((int32_t)b);
+      uoffL_h.push_back(uoff_h.back());
+      aoffL_h.push_back(aoffL_h.back() + 2 * (int64_t)n * n);
     }
+    urep_h.push_back((int32_t)b);
+    uoff_h.push_back(uoff_h.back() + (int64_t)n * n);
+  }
+  const int64_t nuniq = (int64_t)urep_h.size();
+  const int64_t nlarge = (int64_t)urepL_h.size();
+  P.nunique = nuniq;
   const int64_t inv_elems = uoff_h.back();
   DBuf<int32_t> urep;
   VC_TRY(urep.alloc(std::max<size_t>(urep_h.size(), 1)));
   VC_TRY(P.uoff.alloc(uoff_h.size()));
   VC_TRY(P.inv_d.alloc((size_t)std::max<int64_t>(inv_elems, 1)));
   VC_TRY(P.inv_f.alloc((size_t)std::max<int64_t>(inv_elems, 1)));
-  VC_CUDA(cudaMemcpyAsync(urep.p, urep_h.data(), sizeof(int32_t) * urep_h.size(), cudaMemcpyHostToDevice, h.stream));
+  if (nuniq > 0)
+    VC_CUDA(cudaMemcpyAsync(urep.p, urep_h.data(), sizeof(int32_t) * urep_h.size(), cudaMemcpyHostToDevice, h.stream));
   VC_CUDA(cudaMemcpyAsync(P.uoff.p, uoff_h.data(), sizeof(int64_t) * uoff_h.size(), cudaMemcpyHostToDevice, h.stream));
-  if (nuniq > 0) {
-    DBuf<double> aug;
-    DBuf<int> status;
-    VC_TRY(aug.alloc((size_t)(2 * inv_elems)));
-    VC_TRY(status.alloc(1));
-    VC_CUDA(cudaMemsetAsync(status.p, 0, sizeof(int), h.stream));
-    ToepTabs tt;
-    for (int kk = 0; kk < kNumKernels; ++kk) {
-      tt.T[kk] = h.toep[kk].p;
-      for (int a = 0; a < 3; ++a) tt.d[kk][a] = h.tdims[kk][a];
-    }
-    tt.n[0] = g.nx; tt.n[1] = g.ny; tt.n[2] = g.nz;
-    k_assemble<<<(unsigned)nuniq, TB, 0, h.stream>>>(tt, urep.p, P.blk_off.p, P.blk_idx.p, P.uoff.p,
-                                                     h.pan.orient.p, h.pan.face.p, h.pan.kind.p,
-                                                     h.pan.idiag.p, aug.p); ::vc::note_launch();
-    {
-      // pivot-column double buffer: one column of n values per unique block
-      std::vector<int64_t> poff_h(nuniq + 1, 0);
-      for (int64_t q = 0; q < nuniq; ++q) poff_h[q + 1] = poff_h[q] + cnt_h[urep_h[q]];
-      DBuf<int64_t> poff;
-      DBuf<double> pbuf;
-      VC_TRY(poff.alloc(poff_h.size()));
-      VC_TRY(pbuf.alloc((size_t)std::max<int64_t>(2 * poff_h.back(), 1)));
-      VC_CUDA(cudaMemcpyAsync(poff.p, poff_h.data(), sizeof(int64_t) * poff_h.size(),
-                              cudaMemcpyHostToDevice, h.stream));
-      const int slabs = (2 * P.max_n + kGJCols - 1) / kGJCols;
-      const size_t sm = sizeof(double) * ((size_t)P.max_n + 2 * kGJCols);
-      if (sm > 48 * 1024)
-        VC_CUDA(cudaFuncSetAttribute(k_gj_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      dim3 grid((unsigned)slabs, (unsigned)nuniq);
-      for (int c = 0; c < P.max_n; ++c) {
-        const double* pin = pbuf.p + (c & 1) * poff_h.back();
-        double* pout = pbuf.p + ((c + 1) & 1) * poff_h.back();
-        k_gj_step<<<grid, TB, sm, h.stream>>>(c, urep.p, P.blk_off.p, P.uoff.p, poff.p, aug.p, pin,
-                                              pout, status.p); ::vc::note_launch();
-      }
-      VC_CUDA(cudaGetLastError());
-      VC_CUDA(cudaStreamSynchronize(h.stream));
-    }
-    k_extract_inv<<<(unsigned)nuniq, TB, 0, h.stream>>>(urep.p, P.blk_off.p, P.uoff.p, aug.p, P.inv_d.p,
-                                                        P.inv_f.p); ::vc::note_launch();
+  DBuf<int> status;
+  VC_TRY(status.alloc(1));
+  VC_CUDA(cudaMemsetAsync(status.p, 0, sizeof(int), h.stream));
+  ToepTabs tt;
+  for (int kk = 0; kk < kNumKernels; ++kk) {
+    tt.T[kk] = h.toep[kk].p;
+    for (int a = 0; a < 3; ++a) tt.d[kk][a] = h.tdims[kk][a];
+  }
+  tt.n[0] = g.nx; tt.n[1] = g.ny; tt.n[2] = g.nz;
+  if (max_small > 0) {
+    // blocks of up to kGJSmemMax panels: one CTA each, whole block in shared memory
+    const size_t sm = sizeof(float) * (size_t)max_small * (max_small | 1);
+    VC_CUDA(cudaFuncSetAttribute(k_block_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_block_inverse<<<(unsigned)nuniq, 1024, sm, h.stream>>>(tt, urep.p, P.blk_off.p, P.blk_idx.p, P.uoff.p,
+                                                             h.pan.orient.p, h.pan.face.p, h.pan.kind.p,
+                                                             h.pan.idiag.p, P.inv_d.p, P.inv_f.p, status.p); ::vc::note_launch();
     VC_CUDA(cudaGetLastError());
-    int st = 0;
-    VC_CUDA(cudaMemcpyAsync(&st, status.p, sizeof(int), cudaMemcpyDeviceToHost, h.stream));
-    VC_CUDA(cudaStreamSynchronize(h.stream));
-    VC_CHECK(st == 0, VOXCAP_ERR_ARG, "singular preconditioner block");
+  }
+  if (nlarge > 0) {
+    // larger blocks: FP64 Gauss-Jordan on [A | I], one launch per elimination step
+    DBuf<int32_t> urepL;
+    DBuf<int64_t> uoffL, aoffL, poff;
+    DBuf<double> aug, pbuf;
+    std::vector<int64_t> poff_h(nlarge + 1, 0);
+    for (int64_t q = 0; q < nlarge; ++q) poff_h[q + 1] = poff_h[q] + (off_h[urepL_h[q] + 1] - off_h[urepL_h[q]]);
+    VC_TRY(urepL.alloc(urepL_h.size()));
+    VC_TRY(uoffL.alloc(uoffL_h.size()));
+    VC_TRY(aoffL.alloc(aoffL_h.size()));
+    VC_TRY(poff.alloc(poff_h.size()));
+    VC_TRY(aug.alloc((size_t)aoffL_h.back()));
+    VC_TRY(pbuf.alloc((size_t)std::max<int64_t>(2 * poff_h.back(), 1)));
+    VC_CUDA(cudaMemcpyAsync(urepL.p, urepL_h.data(), sizeof(int32_t) * urepL_h.size(), cudaMemcpyHostToDevice, h.stream));
+    VC_CUDA(cudaMemcpyAsync(uoffL.p, uoffL_h.data(), sizeof(int64_t) * uoffL_h.size(), cudaMemcpyHostToDevice, h.stream));
+    VC_CUDA(cudaMemcpyAsync(aoffL.p, aoffL_h.data(), sizeof(int64_t) * aoffL_h.size(), cudaMemcpyHostToDevice, h.stream));
+    VC_CUDA(cudaMemcpyAsync(poff.p, poff_h.data(), sizeof(int64_t) * poff_h.size(), cudaMemcpyHostToDevice, h.stream));
+    k_assemble<<<(unsigned)nlarge, TB, 0, h.stream>>>(tt, urepL.p, P.blk_off.p, P.blk_idx.p, aoffL.p,
+                                                      h.pan.orient.p, h.pan.face.p, h.pan.kind.p,
+                                                      h.pan.idiag.p, aug.p); ::vc::note_launch();
+    const int slabs = (2 * max_large + kGJCols - 1) / kGJCols;
+    const size_t sm = sizeof(double) * ((size_t)max_large + 2 * kGJCols);
+    if (sm > 48 * 1024)
+      VC_CUDA(cudaFuncSetAttribute(k_gj_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    dim3 grid((unsigned)slabs, (unsigned)nlarge);
+    for (int c = 0; c < max_large; ++c) {
+      const double* pin = pbuf.p + (c & 1) * poff_h.back();
+      double* pout = pbuf.p + ((c + 1) & 1) * poff_h.back();
+      k_gj_step<<<grid, TB, sm, h.stream>>>(c, urepL.p, P.blk_off.p, aoffL.p, poff.p, aug.p, pin,
+                                            pout, status.p); ::vc::note_launch();
+    }
+    VC_CUDA(cudaGetLastError());
+    k_extract_inv<<<(unsigned)nlarge, TB, 0, h.stream>>>(urepL.p, P.blk_off.p, aoffL.p, uoffL.p, aug.p,
+                                                         P.inv_d.p, P.inv_f.p); ::vc::note_launch();
+    VC_CUDA(cudaGetLastError());
   }
   DBuf<int32_t> inblk;
   VC_TRY(inblk.alloc((size_t)std::max<int64_t>(N, 1)));
@@ -526,7 +659,10 @@ int build_precond(Handle& h) {
   k_diag_scale<<<(unsigned)((N + TB - 1) / TB), TB, 0, h.stream>>>(
       N, P.kind, h.pan.kind.p, h.pan.idiag.p, pself, inblk.p, P.dscale_d.p, P.dscale_f.p); ::vc::note_launch();
   VC_CUDA(cudaGetLastError());
+  int st = 0;
+  VC_CUDA(cudaMemcpyAsync(&st, status.p, sizeof(int), cudaMemcpyDeviceToHost, h.stream));
   VC_CUDA(cudaStreamSynchronize(h.stream));
+  VC_CHECK(st == 0, VOXCAP_ERR_ARG, "singular preconditioner block");
   return VOXCAP_OK;
 }
 

@@ -21,6 +21,7 @@ F32, F64 = 0, 1
 MV_PRECOND, MV_ADJOINT, MV_RONLY = 1, 2, 4
 FP64, FP32_REFINE = 0, 1
 PRECOND = {"bdd": 0, "bd": 1, "diag": 2, "none": 3}
+ENTRIES = {"auto": 0, "fp64": 1, "far32": 2}
 EPS0 = 8.8541878128e-12
 
 # exported symbols, in header order (checked by the CPU tests)
@@ -41,7 +42,7 @@ class Opts(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("max_iters", ctypes.c_int),
                 ("max_sweeps", ctypes.c_int), ("nv", ctypes.c_int * 3),
                 ("precond", ctypes.c_int), ("pad_mode", ctypes.c_int),
-                ("tucker", ctypes.POINTER(Tucker))]
+                ("entries", ctypes.c_int), ("tucker", ctypes.POINTER(Tucker))]
 
 
 class Stats(ctypes.Structure):
@@ -121,6 +122,8 @@ def default_opts(**kw) -> Opts:
                 o.tucker = ctypes.pointer(t)
         elif k == "precision" and isinstance(v, str):
             o.precision = {"fp64": FP64, "fp32_refine": FP32_REFINE}[v]
+        elif k == "entries" and isinstance(v, str):
+            o.entries = ENTRIES[v]
         else:
             setattr(o, k, v)
     return o

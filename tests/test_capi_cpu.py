@@ -67,12 +67,13 @@ def test_struct_layouts_match_header(tmp_path, libpath):
     from paper_2004_02609_gb300 import voxcap as V
     src = tmp_path / "sz.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "voxcap.h"\n'
-                   'int main(){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(voxcap_opts), '
+                   'int main(){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(voxcap_opts), '
                    'sizeof(voxcap_stats), sizeof(voxcap_tucker), offsetof(voxcap_opts, tucker), '
-                   'offsetof(voxcap_opts, pad_mode), offsetof(voxcap_tucker, factor));return 0;}\n')
+                   'offsetof(voxcap_opts, pad_mode), offsetof(voxcap_opts, entries), '
+                   'offsetof(voxcap_tucker, factor));return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     want = [ctypes.sizeof(V.Opts), ctypes.sizeof(V.Stats), ctypes.sizeof(V.Tucker),
-            V.Opts.tucker.offset, V.Opts.pad_mode.offset, V.Tucker.factor.offset]
+            V.Opts.tucker.offset, V.Opts.pad_mode.offset, V.Opts.entries.offset, V.Tucker.factor.offset]
     assert got == want

@@ -37,10 +37,13 @@ def bus():
 
 
 def test_bus_crossing_sampled_product(bus):
-    """y = A x at full size (110,848 panels) for a sparse x: sampled rows
-    against sums of oracle integrals."""
+    """y = A x at full size (110,848 panels) for a sparse x, FP64 entries and
+    products: sampled rows against sums of oracle integrals."""
     import torch
-    w, vc = bus
+    from paper_2004_02609_gb300 import voxcap as V
+    w, _ = bus
+    vc = V.VoxCap(torch.tensor(w.labels, device="cuda"), w.conductor_id, w.eps_r, w.voxel_size,
+                  entries="fp64")
     pm = vc.panel_map()
     ps = O.panels(w.labels, w.conductor_id, w.eps_r)
     assert np.array_equal(pm["face"], ps.face) and np.array_equal(pm["kind"], ps.kind)
@@ -62,9 +65,10 @@ def test_bus_crossing_sampled_product(bus):
 
 
 def test_bus_crossing_capacitance_fp32_refine_vs_fp64(bus):
-    """8 conductor right-hand sides in one batch: FP32 products with FP64
-    refinement agree with the plain FP64 solve to 1e-4 (the target) and
-    the matrix has the capacitance properties."""
+    """8 conductor right-hand sides in one batch: FP32 products (FP32
+    far-field entries) with FP64 refinement agree with the plain FP64 solve
+    (FP64 entries) to 1e-4 (the target) and the matrix has the capacitance
+    properties."""
     w, vc = bus
     C32, st = vc.capacitance(tol=1e-6)
     assert st["converged"] == 1 and C32.shape == (8, 8)

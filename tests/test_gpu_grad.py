@@ -35,7 +35,7 @@ def test_gradient_matches_dense_adjoint(precision):
     lab, cid, eps = _tiny(0)
     G = np.array([[1.0, 0.3], [-0.7, 2.0]])
     gref, Cref = O.capacitance_grad(lab, cid, eps, G, voxel_size=1e-6, rtol=1e-13)
-    vc = V.VoxCap(lab, cid, eps, 1e-6, precision=precision, nv=3)
+    vc = V.VoxCap(lab, cid, eps, 1e-6, precision=precision, nv=3, entries="fp64")
     C, _ = vc.capacitance(tol=1e-11)
     g, _ = vc.capacitance_grad(G, tol=1e-11)
     assert np.max(np.abs(C - Cref)) < 1e-7 * np.max(np.abs(Cref))
