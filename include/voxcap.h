@@ -67,7 +67,9 @@ extern "C" {
 #define VOXCAP_ENTRIES_AUTO 0    /* FP32 far field under VOXCAP_FP32_REFINE, FP64 under VOXCAP_FP64 */
 #define VOXCAP_ENTRIES_FP64 1    /* every entry in FP64 (near-field closed forms, far-field quadrature) */
 #define VOXCAP_ENTRIES_FAR32 2   /* near-field closed forms in FP64, far-field quadrature sums in FP32
-                                    (entries to about 1e-7 relative, the FP32 products' accuracy) */
+                                    (entries to about 1e-7 relative, the FP32 products' accuracy);
+                                    the kernel spectra are then transformed in FP32 as well and the
+                                    FP64 products use their widening */
 
 /* dtypes of voxcap_matvec */
 #define VOXCAP_F32 0

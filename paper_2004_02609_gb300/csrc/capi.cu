@@ -66,6 +66,8 @@ static int setup_impl(const int32_t* labels, int nx, int ny, int nz, int n_struc
   if (h.opts.max_iters < 1) h.opts.max_iters = 2000;
   VC_CHECK(h.opts.entries >= VOXCAP_ENTRIES_AUTO && h.opts.entries <= VOXCAP_ENTRIES_FAR32, VOXCAP_ERR_ARG,
            "entries must be one of VOXCAP_ENTRIES_*");
+  h.far32 = h.opts.entries == VOXCAP_ENTRIES_FAR32 ||
+            (h.opts.entries == VOXCAP_ENTRIES_AUTO && h.opts.precision == VOXCAP_FP32_REFINE);
   h.dv = voxel_size_m;
   h.nlab = n_labels;
   h.cid.assign(conductor_id, conductor_id + n_labels);

@@ -396,6 +396,7 @@ __global__ void k_toeplitz(ToepLaunch L) {
   if (gi < 3) {
     const int al = gi;
     const int a1 = al == 0 ? 1 : 0, a2 = al == 2 ? 1 : 2;
+    if (e[al] <= 1 && e[a1] <= 2 && e[a2] <= 2) return;     // near field: k_toeplitz_near
     double P, E;
     par_pe((double)e[al], (double)e[a1], (double)e[a2], &P, &E, L.far32 != 0);
     L.out[al][q] = P;
@@ -403,11 +404,83 @@ __global__ void k_toeplitz(ToepLaunch L) {
   } else {
     const int pair = gi - 3;
     const int al = pair == 2 ? 1 : 0, be = pair == 0 ? 1 : 2, ga = 3 - al - be;
+    if (e[al] <= 1 && e[be] <= 1 && e[ga] <= 2) return;      // near field: k_toeplitz_near
     double P, Ea, Eb;
     ort_pe(e[al] + 0.5, e[be] + 0.5, (double)e[ga], &P, &Ea, &Eb, L.far32 != 0);
     L.out[3 + pair][q] = P;
     L.out[9 + pair][q] = Ea;
     L.out[12 + pair][q] = Eb;
+  }
+}
+
+// The near-field entries (gap <= 1 voxel: closed-form corner sums in FP64),
+// one warp per entry and one lane per corner term.  Blocks 0..53: parallel
+// groups, offsets (h, s, t) in {0,1} x {0,1,2}^2; blocks 54..89: orthogonal
+// groups, Toeplitz offsets {0,1}^2 x {0,1,2}.
+constexpr int kNearBlocks = 3 * 18 + 3 * 12;
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void k_toeplitz_near(ToepLaunch L) {
+  const int b = blockIdx.x, lane = threadIdx.x;
+  int gi, e[3];
+  if (b < 54) {
+    gi = b / 18;
+    const int r = b % 18, al = gi, a1 = al == 0 ? 1 : 0, a2 = al == 2 ? 1 : 2;
+    e[al] = r / 9;
+    e[a1] = (r / 3) % 3;
+    e[a2] = r % 3;
+  } else {
+    gi = 3 + (b - 54) / 12;
+    const int r = (b - 54) % 12, pair = gi - 3;
+    const int al = pair == 2 ? 1 : 0, be = pair == 0 ? 1 : 2, ga = 3 - al - be;
+    e[al] = r / 6;
+    e[be] = (r / 3) % 2;
+    e[ga] = r % 3;
+  }
+  for (int a = 0; a < 3; ++a)
+    if (e[a] >= L.d[gi][a]) return;                  // offset outside this grid's tables
+  const int64_t q = (int64_t)e[0] + (int64_t)L.d[gi][0] * (e[1] + (int64_t)L.d[gi][1] * e[2]);
+  if (gi < 3) {
+    const int al = gi, a1 = al == 0 ? 1 : 0, a2 = al == 2 ? 1 : 2;
+    const double h = e[al], s = e[a1], t = e[a2];
+    double vp = 0.0, ve = 0.0;
+    if (lane < 18) {
+      const int m = lane % 9, i = m / 3, j = m % 3;
+      const double wgt = c_cw[i] * c_cw[j];
+      const double u = s + (i - 1), v = t + (j - 1);
+      if (lane < 9) vp = wgt * F_par(u, v, h);
+      else if (h != 0.0) ve = wgt * Fh_par(u, v, h);
+    }
+    vp = warp_sum(vp);
+    ve = warp_sum(ve);
+    if (lane == 0) {
+      L.out[al][q] = vp * kInv4Pi;
+      L.out[6 + al][q] = ve * kInv4Pi;
+    }
+  } else {
+    const int pair = gi - 3;
+    const int al = pair == 2 ? 1 : 0, be = pair == 0 ? 1 : 2, ga = 3 - al - be;
+    const double A = e[al] + 0.5, B = e[be] + 0.5, Cc = e[ga];
+    double acc[3] = {0.0, 0.0, 0.0};                 // P, Ea, Eb
+    for (int m = lane; m < 36; m += 32) {
+      const int comp = m / 12, idx = m % 12;
+      const int s1 = (idx & 1) ? 1 : -1, s2 = (idx & 2) ? 1 : -1, j = idx / 4;
+      const double wgt = (double)(s1 * s2) * c_cw[j];
+      const double w = Cc + (j - 1);
+      if (comp == 0) acc[0] += wgt * H_ort(A + 0.5 * s1, B + 0.5 * s2, w);
+      else if (comp == 1) acc[1] += wgt * Hp_ort(A + 0.5 * s1, B + 0.5 * s2, w);
+      else acc[2] += wgt * Hp_ort(B + 0.5 * s1, A + 0.5 * s2, w);
+    }
+    for (int c = 0; c < 3; ++c) acc[c] = warp_sum(acc[c]);
+    if (lane == 0) {
+      L.out[3 + pair][q] = acc[0] * kInv4Pi;
+      L.out[9 + pair][q] = acc[1] * kInv4Pi;
+      L.out[12 + pair][q] = acc[2] * kInv4Pi;
+    }
   }
 }
 
@@ -434,11 +507,11 @@ int build_toeplitz(Handle& h) {
     for (int a = 0; a < 3; ++a) L.d[gi][a] = d[a];
     L.start[gi + 1] = L.start[gi] + (int64_t)d[0] * d[1] * d[2];
   }
-  L.far32 = h.opts.entries == VOXCAP_ENTRIES_FAR32 ||
-            (h.opts.entries == VOXCAP_ENTRIES_AUTO && h.opts.precision == VOXCAP_FP32_REFINE);
+  L.far32 = h.far32 ? 1 : 0;
   const int TB = 128;
   const int64_t tot = L.start[6];
   k_toeplitz<<<(unsigned)((tot + TB - 1) / TB), TB, 0, h.stream>>>(L); ::vc::note_launch();
+  k_toeplitz_near<<<kNearBlocks, 32, 0, h.stream>>>(L); ::vc::note_launch();
   VC_CUDA(cudaGetLastError());
   return VOXCAP_OK;
 }

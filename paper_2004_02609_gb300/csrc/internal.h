@@ -116,6 +116,9 @@ struct Handle {
   int device = 0;
   cudaStream_t stream = nullptr;
   voxcap_opts opts;
+  // the operator is only FP32-accurate (FP32 far-field entries): its spectra
+  // are transformed in FP32 too and the FP64 copy is their widening
+  bool far32 = false;
   double dv = 1.0;
   int nlab = 0;
   std::vector<int32_t> cid;

@@ -142,19 +142,26 @@ __device__ __forceinline__ uint64_t pat_key(const BoxGeom& bg, int64_t gb, int p
   return key;
 }
 
+// hash of a box's pattern: the sum of its mixed panel keys (order-free; the
+// representative search below compares patterns exactly).  One warp per box.
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
 __global__ void k_box_hash(BoxGeom bg, int64_t nboxes, const int32_t* offs, const int32_t* idx,
                            const int8_t* orient, const int32_t* face, const int8_t* kind,
                            const double* idiag, int mode, uint64_t* hash) {
-  int64_t gb = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gb >= nboxes) return;
-  uint64_t hsh = 1469598103934665603ull;
-  for (int q = offs[gb]; q < offs[gb + 1]; ++q) {
-    uint64_t k = pat_key(bg, gb, idx[q], orient, face, kind, idiag, mode);
-    hsh ^= k;
-    hsh *= 1099511628211ull;
-    hsh ^= hsh >> 29;
-  }
-  hash[gb] = hsh;
+  const int64_t gb = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (gb >= nboxes) return;                          // whole warps leave together
+  uint64_t hsh = 0;
+  for (int q = offs[gb] + lane; q < offs[gb + 1]; q += 32)
+    hsh += mix64(pat_key(bg, gb, idx[q], orient, face, kind, idiag, mode));
+  for (int o = 16; o > 0; o >>= 1) hsh += __shfl_down_sync(0xffffffffu, hsh, o);
+  if (lane == 0) hash[gb] = hsh + (uint64_t)(offs[gb + 1] - offs[gb]);
 }
 
 // representative = lowest-index box with the same pattern (exact comparison)
@@ -272,111 +279,148 @@ __global__ void k_assemble(ToepTabs tt, const int32_t* urep, const int32_t* offs
   }
 }
 
-// Inverse of one unique block held whole in shared memory (FP32; the
-// preconditioner only steers GMRES, the solution's accuracy comes from the
-// residuals).  In-place Gauss-Jordan with pivot bookkeeping: step k takes
-// as pivot the unused row p_k with the largest |S[p][k]|, scales that row and
-// eliminates column k from every other row; column k, now a unit vector,
-// stores column p_k of the inverse-to-be.  After n steps
-// A^-1[k][j] = S[p_k][q_j] with q the inverse permutation of p.
-constexpr int kGJSmemMax = 224;
+// Inverse of one unique block of n <= 32 RA panels held in registers by
+// one CTA of 16 warps (FP32; the preconditioner only steers GMRES, the
+// solution's accuracy comes from the residuals).  Thread (warp w, lane l)
+// holds rows i = l + 32 a and columns j = w + 16 b.  In-place Gauss-Jordan
+// with pivot bookkeeping: step k takes as pivot the unused row p_k with the
+// largest |S[p][k]|, scales that row and eliminates column k from every
+// other row; column k, now a unit vector, stores column p_k of the
+// inverse-to-be, and A^-1[q_i][p_j] = S[i][j] at the end (q = p^-1).  The
+// warp owning column k finds the pivot from its own registers and publishes
+// the column through shared memory (double-buffered by step parity), row p
+// reaches the other lanes of each warp by shuffles: one barrier per step.
+constexpr int kGJTileMax = 224;
+constexpr int kGJWarps = 16;
 
-__global__ void __launch_bounds__(1024) k_block_inverse(ToepTabs tt, const int32_t* __restrict__ urep,
-                                                        const int32_t* __restrict__ offs,
-                                                        const int32_t* __restrict__ idx,
-                                                        const int64_t* __restrict__ uoff,
-                                                        const int8_t* __restrict__ orient,
-                                                        const int32_t* __restrict__ face,
-                                                        const int8_t* __restrict__ kind,
-                                                        const double* __restrict__ idiag,
-                                                        double* __restrict__ inv_d, float* __restrict__ inv_f,
-                                                        int* __restrict__ status) {
-  extern __shared__ float S[];                       // n rows of stride ld (odd)
-  __shared__ float colb[2][kGJSmemMax], rowb[2][kGJSmemMax];
-  __shared__ int perm[kGJSmemMax], qinv[kGJSmemMax];
-  __shared__ unsigned char used[kGJSmemMax];
-  __shared__ int piv_row[2];
-  __shared__ float piv_inv[2];
+template <int RA>
+__global__ void __launch_bounds__(32 * kGJWarps, 1)
+k_block_inverse(ToepTabs tt, const int32_t* __restrict__ urep, const int32_t* __restrict__ offs,
+                const int32_t* __restrict__ idx, const int64_t* __restrict__ uoff,
+                const int8_t* __restrict__ orient, const int32_t* __restrict__ face,
+                const int8_t* __restrict__ kind, const double* __restrict__ idiag,
+                double* __restrict__ inv_d, float* __restrict__ inv_f, int* __restrict__ status) {
+  constexpr int CB = 2 * RA;
+  constexpr int NMAX = 32 * RA;
+  __shared__ float colb[2][NMAX];
+  __shared__ int prow[2];
+  __shared__ float pinv[2];
+  __shared__ int perm[NMAX], qinv[NMAX];
   __shared__ int fail;
   const int u = blockIdx.x;
   const int gb = urep[u];
   const int q0 = offs[gb];
   const int n = offs[gb + 1] - q0;
-  if (n > kGJSmemMax || n == 0) return;              // larger blocks take the multi-CTA path
-  const int ld = n | 1;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
-  for (int t = tid; t < n * n; t += nt) {
-    const int i = t / n, j = t - (t / n) * n;
-    const int pk = idx[q0 + i], pl = idx[q0 + j];
-    int ck[3], cl[3];
-    face_coords(tt.n, orient[pk], face[pk], ck);
-    face_coords(tt.n, orient[pl], face[pl], cl);
-    const bool E = kind[pk] == 1;
-    double v = a_entry(tt, E, orient[pk], ck, orient[pl], cl);
-    if (E && i == j) v += idiag[pk];
-    S[i * ld + j] = (float)v;
+  if (n > NMAX || n == 0) return;                    // larger blocks take the multi-CTA path
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float S[RA][CB];
+#pragma unroll
+  for (int a = 0; a < RA; ++a) {
+    const int i = lane + 32 * a;
+    int ck[3] = {0, 0, 0}, pk = 0;
+    if (i < n) {
+      pk = idx[q0 + i];
+      face_coords(tt.n, orient[pk], face[pk], ck);
+    }
+#pragma unroll
+    for (int b = 0; b < CB; ++b) {
+      const int j = w + kGJWarps * b;
+      float v = 0.0f;
+      if (i < n && j < n) {
+        const int pl = idx[q0 + j];
+        int cl[3];
+        face_coords(tt.n, orient[pl], face[pl], cl);
+        const bool E = kind[pk] == 1;
+        double e = a_entry(tt, E, orient[pk], ck, orient[pl], cl);
+        if (E && i == j) e += idiag[pk];
+        v = (float)e;
+      }
+      S[a][b] = v;
+    }
   }
-  for (int i = tid; i < n; i += nt) used[i] = 0;
-  if (tid == 0) fail = 0;
-  __syncthreads();
+  if (threadIdx.x == 0) fail = 0;
+  unsigned used = 0;                                 // bit a: row lane + 32 a already a pivot
   for (int k = 0; k < n; ++k) {
-    const int b = k & 1;
-    if (wid == 0) {                                  // pivot search over the unused rows
+    const int par = k & 1;
+    if (w == k % kGJWarps) {                         // pivot search in the owner of column k
+      const int bk = k / kGJWarps;
       float best = -1.0f;
       int bi = n;
-      for (int i = lane; i < n; i += 32) {
-        const float v = S[i * ld + k];
-        colb[b][i] = v;
-        if (!used[i] && fabsf(v) > best) { best = fabsf(v); bi = i; }
+#pragma unroll
+      for (int a = 0; a < RA; ++a) {
+        const int i = lane + 32 * a;
+        float v = 0.0f;
+#pragma unroll
+        for (int b = 0; b < CB; ++b)
+          if (b == bk) v = S[a][b];
+        if (i < n) {
+          colb[par][i] = v;
+          if (!((used >> a) & 1u) && fabsf(v) > best) { best = fabsf(v); bi = i; }
+        }
       }
       for (int d = 16; d > 0; d >>= 1) {
         const float ob = __shfl_down_sync(0xffffffffu, best, d);
         const int oi = __shfl_down_sync(0xffffffffu, bi, d);
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
+      __syncwarp();
       if (lane == 0) {
         if (!(best > 0.0f) || bi >= n) {
           fail = 1;
           bi = 0;
-          best = 1.0f;
         }
-        piv_row[b] = bi;
-        piv_inv[b] = 1.0f / colb[b][bi];
-        used[bi] = 1;
+        prow[par] = bi;
+        pinv[par] = 1.0f / colb[par][bi];
         perm[k] = bi;
       }
     }
     __syncthreads();
     if (fail) break;                                 // uniform: read after the barrier
-    const int p = piv_row[b];
-    const float ip = piv_inv[b];
-    for (int j = tid; j < n; j += nt) rowb[b][j] = (j == k ? 1.0f : S[p * ld + j]) * ip;
-    __syncthreads();
-    for (int i = wid; i < n; i += nw) {
-      float* row = S + i * ld;
-      if (i == p) {
-        for (int j = lane; j < n; j += 32) row[j] = rowb[b][j];
-      } else {
-        const float f = colb[b][i];
-        for (int j = lane; j < n; j += 32) row[j] = (j == k ? 0.0f : row[j]) - f * rowb[b][j];
+    const int p = prow[par];
+    const float ip = pinv[par];
+    const int lp = p & 31, ap = p >> 5;
+    if (lane == lp) used |= 1u << ap;
+    float rp[CB];                                    // row p, scaled, in this thread's columns
+#pragma unroll
+    for (int b = 0; b < CB; ++b) {
+      float v = 0.0f;
+#pragma unroll
+      for (int a = 0; a < RA; ++a)
+        if (a == ap) v = S[a][b];
+      v = __shfl_sync(0xffffffffu, v, lp);
+      rp[b] = ((w + kGJWarps * b) == k ? 1.0f : v) * ip;
+    }
+#pragma unroll
+    for (int a = 0; a < RA; ++a) {
+      const int i = lane + 32 * a;
+      const float f = i < n ? colb[par][i] : 0.0f;
+#pragma unroll
+      for (int b = 0; b < CB; ++b) {
+        const int j = w + kGJWarps * b;
+        if (i == p) S[a][b] = rp[b];
+        else S[a][b] = (j == k ? 0.0f : S[a][b]) - f * rp[b];
       }
     }
-    __syncthreads();
   }
+  __syncthreads();
   if (fail) {
-    if (tid == 0) atomicExch(status, 1);
+    if (threadIdx.x == 0) atomicExch(status, 1);
     return;
   }
-  for (int k = tid; k < n; k += nt) qinv[perm[k]] = k;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) qinv[perm[k]] = k;
   __syncthreads();
   const int64_t o = uoff[u];
-  for (int t = tid; t < n * n; t += nt) {
-    const int k = t / n, j = t - (t / n) * n;
-    const float v = S[perm[k] * ld + qinv[j]];
-    inv_f[o + t] = v;
-    inv_d[o + t] = (double)v;
-  }
+#pragma unroll
+  for (int a = 0; a < RA; ++a)
+#pragma unroll
+    for (int b = 0; b < CB; ++b) {
+      const int i = lane + 32 * a, j = w + kGJWarps * b;
+      if (i < n && j < n) {
+        const int64_t t = o + (int64_t)qinv[i] * n + perm[j];
+        inv_f[t] = S[a][b];
+        inv_d[t] = (double)S[a][b];
+      }
+    }
 }
 
 // Gauss-Jordan with partial pivoting on [A | I] -> [I | A^-1], one launch
@@ -545,7 +589,7 @@ int build_precond(Handle& h) {
   VC_TRY(rep_scan.alloc((size_t)nboxes + 1));
   int32_t* isrep = meta.p + nboxes + 1;
   unsigned nbk = (unsigned)((nboxes + TB - 1) / TB);
-  k_box_hash<<<nbk, TB, 0, h.stream>>>(bg, nboxes, P.blk_off.p, P.blk_idx.p, h.pan.orient.p,
+  k_box_hash<<<(unsigned)((nboxes * 32 + TB - 1) / TB), TB, 0, h.stream>>>(bg, nboxes, P.blk_off.p, P.blk_idx.p, h.pan.orient.p,
                                        h.pan.face.p, h.pan.kind.p, h.pan.idiag.p, P.kind, hash.p); ::vc::note_launch();
   k_box_rep<<<nbk, TB, 0, h.stream>>>(bg, nboxes, P.blk_off.p, P.blk_idx.p, h.pan.orient.p,
                                       h.pan.face.p, h.pan.kind.p, h.pan.idiag.p, P.kind, hash.p,
@@ -574,7 +618,7 @@ int build_precond(Handle& h) {
     const int n = off_h[b + 1] - off_h[b];
     P.max_n = std::max(P.max_n, n);
     if (!isrep_h[b]) continue;
-    if (n <= kGJSmemMax) {
+    if (n <= kGJTileMax) {
       max_small = std::max(max_small, n);
     } else {
       max_large = std::max(max_large, n);
@@ -607,12 +651,20 @@ int build_precond(Handle& h) {
   }
   tt.n[0] = g.nx; tt.n[1] = g.ny; tt.n[2] = g.nz;
   if (max_small > 0) {
-    // blocks of up to kGJSmemMax panels: one CTA each, whole block in shared memory
-    const size_t sm = sizeof(float) * (size_t)max_small * (max_small | 1);
-    VC_CUDA(cudaFuncSetAttribute(k_block_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_block_inverse<<<(unsigned)nuniq, 1024, sm, h.stream>>>(tt, urep.p, P.blk_off.p, P.blk_idx.p, P.uoff.p,
-                                                             h.pan.orient.p, h.pan.face.p, h.pan.kind.p,
-                                                             h.pan.idiag.p, P.inv_d.p, P.inv_f.p, status.p); ::vc::note_launch();
+    // blocks of up to kGJTileMax panels: one CTA each, the block in registers
+    const int RA = (max_small + 31) / 32;
+#define VC_BINV(R)                                                                                  \
+  case R:                                                                                           \
+    k_block_inverse<R><<<(unsigned)nuniq, 32 * kGJWarps, 0, h.stream>>>(                            \
+        tt, urep.p, P.blk_off.p, P.blk_idx.p, P.uoff.p, h.pan.orient.p, h.pan.face.p, h.pan.kind.p,  \
+        h.pan.idiag.p, P.inv_d.p, P.inv_f.p, status.p);                                             \
+    break;
+    switch (RA) {
+      VC_BINV(1) VC_BINV(2) VC_BINV(3) VC_BINV(4) VC_BINV(5) VC_BINV(6) VC_BINV(7)
+      default: VC_CHECK(false, VOXCAP_ERR_UNSUPPORTED, "block too large for the register inverse");
+    }
+#undef VC_BINV
+    ::vc::note_launch();
     VC_CUDA(cudaGetLastError());
   }
   if (nlarge > 0) {
@@ -675,6 +727,11 @@ __global__ void k_pre_diag(int64_t N, int nrhs, const T* __restrict__ ds, const 
   z[t] = ds[t % N] * r[t];
 }
 
+// z_B = R_B r_B for one box (blockIdx.x), one column (blockIdx.y) and the
+// rows [32 blockIdx.z, 32 blockIdx.z + 32) of its block; accumulation in T
+// (the FP32 inner solve's preconditioner needs no FP64 sums).
+constexpr int kPreRows = 32;
+
 template <typename T>
 __global__ void k_pre_blocks(int64_t N, const int32_t* __restrict__ offs, const int32_t* __restrict__ idx,
                              const int32_t* __restrict__ uid, const int64_t* __restrict__ uoff,
@@ -685,19 +742,21 @@ __global__ void k_pre_blocks(int64_t N, const int32_t* __restrict__ offs, const 
   const int rhs = blockIdx.y;
   const int q0 = offs[gb];
   const int n = offs[gb + 1] - q0;
-  if (n == 0) return;
+  const int i0 = blockIdx.z * kPreRows;
+  if (i0 >= n) return;
   const T* Minv = inv + uoff[uid[gb]];
   const T* rr = r + (int64_t)rhs * N;
   T* zz = z + (int64_t)rhs * N;
   for (int j = threadIdx.x; j < n; j += blockDim.x) rv[j] = rr[idx[q0 + j]];
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = wid; i < n; i += nw) {
-    double acc = 0.0;
+  const int i1 = min(n, i0 + kPreRows);
+  for (int i = i0 + wid; i < i1; i += nw) {
+    T acc = (T)0;
     const T* row = Minv + (int64_t)i * n;
-    for (int j = lane; j < n; j += 32) acc += (double)row[j] * (double)rv[j];
+    for (int j = lane; j < n; j += 32) acc += row[j] * rv[j];
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0) zz[idx[q0 + i]] = (T)acc;
+    if (lane == 0) zz[idx[q0 + i]] = acc;
   }
 }
 
@@ -720,8 +779,8 @@ int precond_apply(Handle& h, const T* r, T* z, int nrhs) {
     size_t sm = sizeof(T) * (size_t)P.max_n;
     if (sm > 48 * 1024)
       VC_CUDA(cudaFuncSetAttribute(k_pre_blocks<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    dim3 grid((unsigned)P.nblocks, nrhs);
-    k_pre_blocks<T><<<grid, TB, sm, h.stream>>>(N, P.blk_off.p, P.blk_idx.p, P.blk_uid.p, P.uoff.p,
+    dim3 grid((unsigned)P.nblocks, nrhs, (unsigned)((P.max_n + kPreRows - 1) / kPreRows));
+    k_pre_blocks<T><<<grid, 128, sm, h.stream>>>(N, P.blk_off.p, P.blk_idx.p, P.blk_uid.p, P.uoff.p,
                                                 inv_of<T>(h), r, z); ::vc::note_launch();
     VC_CUDA(cudaGetLastError());
   }

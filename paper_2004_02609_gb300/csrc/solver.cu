@@ -13,6 +13,7 @@
 // Refinement: r = b - A x in FP64 (FP64 product), inner GMRES on A d = r in
 // FP32 (or FP64 for the plain path), x += d, until ||b - A x|| <= tol ||b||
 // per column.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <vector>
@@ -231,8 +232,13 @@ struct SolveCounters {
   int matvecs = 0;
 };
 
-static int nchunks_for(int64_t N) {
+// chunks per column of the dot/update sweeps: at least one per 1024 rows,
+// and for small systems enough (down to 128 rows each) to cover about 304
+// CTAs over all columns -- the FP64 inner products run at a low per-SM rate
+static int nchunks_for(int64_t N, int nrhs) {
   int64_t c = (N + 1023) / 1024;
+  const int64_t fine = std::min<int64_t>((N + 127) / 128, (304 + nrhs - 1) / std::max(nrhs, 1));
+  c = std::max(c, fine);
   if (c < 1) c = 1;
   if (c > 2048) c = 2048;
   return (int)c;
@@ -352,7 +358,7 @@ static int gmres(Handle& h, const T* r, T* d, int nrhs, double rtol, int max_it,
   const int64_t N = h.pan.N;
   const int m = std::max(1, h.opts.restart);
   cudaStream_t st = h.stream;
-  const int nch = nchunks_for(N);
+  const int nch = nchunks_for(N, nrhs);
   const size_t nV = (size_t)(m + 1) * nrhs * N;
   const size_t nW = (size_t)nrhs * N;
   size_t bytes = sizeof(T) * (nV + 3 * nW) + 256;
@@ -526,7 +532,7 @@ static int gmres(Handle& h, const T* r, T* d, int nrhs, double rtol, int max_it,
 static int col_norms(Handle& h, const double* v, int nrhs, std::vector<double>& out, double* partial_ws,
                      double* dev_out) {
   const int64_t N = h.pan.N;
-  const int nch = nchunks_for(N);
+  const int nch = nchunks_for(N, nrhs);
   dim3 g(nch, nrhs);
   k_gs_sweep<double><<<g, kDotTB, 0, h.stream>>>(nullptr, const_cast<double*>(v), N, nrhs, 0, nullptr, 0,
                                                  0, true, nullptr, nch, partial_ws, 1); ::vc::note_launch();
@@ -555,7 +561,7 @@ int solve(Handle& h, const double* B, int nrhs, double tol, double* X, voxcap_st
   const size_t n = (size_t)N * nrhs;
   VC_TRY(R64.alloc(n));
   VC_TRY(AX.alloc(n));
-  VC_TRY(dpart.alloc((size_t)nrhs * nchunks_for(N) + 1));
+  VC_TRY(dpart.alloc((size_t)nrhs * nchunks_for(N, nrhs) + 1));
   VC_TRY(dnorm.alloc(nrhs));
   VC_TRY(fac.alloc(nrhs));
   if (refine) { VC_TRY(rf.alloc(n)); VC_TRY(df.alloc(n)); }

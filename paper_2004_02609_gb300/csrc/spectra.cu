@@ -53,12 +53,37 @@ static int pick_length(int N, int mode) {
   return best;
 }
 
+// cos and sin of 2 pi m / n in double, the angle reduced exactly in integers
+// to at most pi/4 before the library call (about one ulp at any m, n).
+static void unit_root(int64_t m, int64_t n, double* c, double* s) {
+  const double half_pi = 1.57079632679489661923132169163975144;
+  int64_t a = (4 * m) % (4 * n);                    // angle = (pi/2) a / n
+  if (a < 0) a += 4 * n;
+  const int q = (int)(a / n);                       // quadrant
+  const int64_t r = a - (int64_t)q * n;             // within-quadrant angle (pi/2) r / n
+  double sp, cp;                                    // sin, cos of the within-quadrant angle
+  if (2 * r <= n) {
+    const double t = half_pi * (double)r / (double)n;
+    sp = std::sin(t);
+    cp = std::cos(t);
+  } else {
+    const double t = half_pi * (double)(n - r) / (double)n;
+    sp = std::cos(t);
+    cp = std::sin(t);
+  }
+  switch (q) {
+    case 0: *c = cp; *s = sp; break;
+    case 1: *c = -sp; *s = cp; break;
+    case 2: *c = -cp; *s = -sp; break;
+    default: *c = sp; *s = -cp; break;
+  }
+}
+
 // Stage twiddles of a radix plan (see Plan1D) and the half-voxel phases
-// exp(+i pi m / L), computed in long double and rounded once.
+// exp(+i pi m / L).
 template <typename C>
 static void fill_tables(std::vector<C>& stw, std::vector<C>& ph, int L, const int* radix, int nst,
                         int* Ns, int* twoff) {
-  const long double pi = 3.141592653589793238462643383279502884L;
   stw.clear();
   int ns = 1;
   for (int s = 0; s < nst; ++s) {
@@ -67,19 +92,21 @@ static void fill_tables(std::vector<C>& stw, std::vector<C>& ph, int L, const in
     twoff[s] = (int)stw.size();
     for (int k = 0; k < ns; ++k)
       for (int r = 1; r < R; ++r) {
-        long double a = -2.0L * pi * (long double)(r * k) / (long double)(ns * R);
+        double cr, si;
+        unit_root(-(int64_t)r * k, (int64_t)ns * R, &cr, &si);     // exp(-2 pi i r k / (ns R))
         C c;
-        c.x = (decltype(C::x))std::cos(a);
-        c.y = (decltype(C::x))std::sin(a);
+        c.x = (decltype(C::x))cr;
+        c.y = (decltype(C::x))si;
         stw.push_back(c);
       }
     ns *= R;
   }
   ph.resize(L);
   for (int m = 0; m < L; ++m) {
-    long double b = pi * (long double)m / (long double)L;
-    ph[m].x = (decltype(C::x))std::cos(b);
-    ph[m].y = (decltype(C::x))std::sin(b);
+    double cr, si;
+    unit_root(m, 2 * (int64_t)L, &cr, &si);                      // exp(+i pi m / L)
+    ph[m].x = (decltype(C::x))cr;
+    ph[m].y = (decltype(C::x))si;
   }
 }
 
@@ -191,18 +218,29 @@ __device__ __forceinline__ bool axis_lookup(const AxisMap& am, int i, int* e, do
   return true;
 }
 
-__global__ void k_embed(const double* __restrict__ T, int tx, int ty, AxisMap ax, AxisMap ay,
-                        AxisMap az, double* __restrict__ circ) {
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int64_t n = (int64_t)ax.M * ay.M * az.M;
-  if (t >= n) return;
-  int i = (int)(t % ax.M), j = (int)((t / ax.M) % ay.M), k = (int)(t / ((int64_t)ax.M * ay.M));
+// tables and index maps of the 15 kernels
+struct EmbedSet {
+  const double* T[kNumKernels];
+  int tx[kNumKernels], ty[kNumKernels];
+  AxisMap ax[kNumKernels], ay[kNumKernels], az[kNumKernels];
+};
+
+// circ[b] = circulant embedding of kernel k0 + b (b = blockIdx.y)
+template <typename T>
+__global__ void k_embed(EmbedSet es, int k0, int64_t Mtot, T* __restrict__ circ) {
+  const int b = blockIdx.y, kk = k0 + b;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= Mtot) return;
+  const AxisMap& ax = es.ax[kk];
+  const AxisMap& ay = es.ay[kk];
+  const AxisMap& az = es.az[kk];
+  const int i = (int)(t % ax.M), j = (int)((t / ax.M) % ay.M), k = (int)(t / ((int64_t)ax.M * ay.M));
   int ex, ey, ez;
   double sg = 1.0;
   double v = 0.0;
   if (axis_lookup(ax, i, &ex, &sg) && axis_lookup(ay, j, &ey, &sg) && axis_lookup(az, k, &ez, &sg))
-    v = sg * T[(int64_t)ex + (int64_t)tx * (ey + (int64_t)ty * ez)];
-  circ[t] = v;
+    v = sg * es.T[kk][(int64_t)ex + (int64_t)es.tx[kk] * (ey + (int64_t)es.ty[kk] * ez)];
+  circ[(int64_t)b * Mtot + t] = (T)v;
 }
 
 static AxisMap axis_map(int kk, int a, int N, int M) {
@@ -285,29 +323,35 @@ __global__ void k_strided_c2c(C_t<T>* __restrict__ data, int64_t outer, int L, i
   }
 }
 
-// Extract the real octant R of one kernel spectrum (see file comment).
-__global__ void k_extract(const double2* __restrict__ spec, Geom g, int kk, bool E, int te, int so,
+// Extract the real octant R of kernel k0 + b (b = blockIdx.y) from its
+// half spectrum (see file comment); phases and scaling in FP64.
+template <typename T>
+__global__ void k_extract(const C_t<T>* __restrict__ spec, int64_t Htot, Geom g, int k0,
                           const double2* __restrict__ phx, const double2* __restrict__ phy,
                           const double2* __restrict__ phz, double scale,
                           double* __restrict__ Rd, float* __restrict__ Rf) {
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int64_t n = (int64_t)g.Hx * g.Oy * g.Oz;
+  const int b = blockIdx.y, kk = k0 + b;
+  const int te = ker_test(kk), so = ker_src(kk);
+  const bool E = kk >= 6;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = (int64_t)g.Hx * g.Oy * g.Oz;
   if (t >= n) return;
-  int kx = (int)(t % g.Hx), ky = (int)((t / g.Hx) % g.Oy), kz = (int)(t / ((int64_t)g.Hx * g.Oy));
-  double2 v = spec[((int64_t)kz * g.My + ky) * g.Hx + kx];
+  const int kx = (int)(t % g.Hx), ky = (int)((t / g.Hx) % g.Oy), kz = (int)(t / ((int64_t)g.Hx * g.Oy));
+  const C_t<T> w = spec[(int64_t)b * Htot + ((int64_t)kz * g.My + ky) * g.Hx + kx];
+  double2 v = make_double2((double)w.x, (double)w.y);
   // undo exp(-i pi k_te/M) S exp(+i pi k_so/M):  multiply by exp(+i pi k_te/M) exp(-i pi k_so/M)
   if (te != so) {
     const double2* pt = te == 0 ? phx : (te == 1 ? phy : phz);
     const double2* ps = so == 0 ? phx : (so == 1 ? phy : phz);
-    int kt = te == 0 ? kx : (te == 1 ? ky : kz);
-    int ks = so == 0 ? kx : (so == 1 ? ky : kz);
+    const int kt = te == 0 ? kx : (te == 1 ? ky : kz);
+    const int ks = so == 0 ? kx : (so == 1 ? ky : kz);
     v = cmul(v, pt[kt]);
     v = cmul(v, cconj(ps[ks]));
   }
   double r = E ? -v.y : v.x;     // S = -i R  ->  R = i S;  Re(i S) = -Im(S)
   r *= scale;
-  Rd[t] = r;
-  Rf[t] = (float)r;
+  Rd[kk * n + t] = r;
+  Rf[kk * n + t] = (float)r;
 }
 
 // largest power-of-two line count (<= maxlines) whose two buffers fit in 96 KB
@@ -319,74 +363,92 @@ template <typename T> static int smem_limit_lines(int L, int maxlines) {
   return p;
 }
 
-int build_spectra(Handle& h) {
+// The spectra of kernels in batches that fit a 512 MB scratch budget, with
+// transforms in T (FP64, or FP32 when the entries themselves are only
+// FP32-accurate: the FP64 copy is then the FP32 spectrum widened).
+template <typename T>
+static int spectra_impl(Handle& h) {
+  using C = C_t<T>;
   const Geom& g = h.g;
   const int n[3] = {g.nx, g.ny, g.nz};
   const int64_t Mtot = (int64_t)g.Mx * g.My * g.Mz;
   const int64_t Htot = (int64_t)g.Hx * g.My * g.Mz;
   const int64_t Otot = (int64_t)g.Hx * g.Oy * g.Oz;
-  DBuf<double> circ;
-  DBuf<double2> spec;
-  VC_TRY(circ.alloc((size_t)Mtot));
-  VC_TRY(spec.alloc((size_t)Htot));
+  const size_t per_kernel = (size_t)Mtot * sizeof(T) + (size_t)Htot * sizeof(C);
+  const int nb = (int)std::max<size_t>(1, std::min<size_t>(kNumKernels, ((size_t)512 << 20) / per_kernel));
+  DBuf<T> circ;
+  DBuf<C> spec;
+  VC_TRY(circ.alloc((size_t)Mtot * nb));
+  VC_TRY(spec.alloc((size_t)Htot * nb));
   VC_TRY(h.spec_d.alloc((size_t)Otot * kNumKernels));
   VC_TRY(h.spec_f.alloc((size_t)Otot * kNumKernels));
+  EmbedSet es;
+  for (int kk = 0; kk < kNumKernels; ++kk) {
+    es.T[kk] = h.toep[kk].p;
+    es.tx[kk] = h.tdims[kk][0];
+    es.ty[kk] = h.tdims[kk][1];
+    es.ax[kk] = axis_map(kk, 0, n[0], g.Mx);
+    es.ay[kk] = axis_map(kk, 1, n[1], g.My);
+    es.az[kk] = axis_map(kk, 2, n[2], g.Mz);
+  }
   const double scale = 1.0 / (double)Mtot;
   const int TB = 256;
-  for (int kk = 0; kk < kNumKernels; ++kk) {
-    AxisMap am[3];
-    for (int a = 0; a < 3; ++a) am[a] = axis_map(kk, a, n[a], a == 0 ? g.Mx : (a == 1 ? g.My : g.Mz));
-    k_embed<<<(unsigned)((Mtot + TB - 1) / TB), TB, 0, h.stream>>>(
-        h.toep[kk].p, h.tdims[kk][0], h.tdims[kk][1], am[0], am[1], am[2], circ.p); ::vc::note_launch();
+  const Plan1D<C>& px = plan_of<T>(h, 0);
+  const Plan1D<C>& py = plan_of<T>(h, 1);
+  const Plan1D<C>& pz = plan_of<T>(h, 2);
+  for (int k0 = 0; k0 < kNumKernels; k0 += nb) {
+    const int nk = std::min(nb, kNumKernels - k0);
+    k_embed<T><<<dim3((unsigned)((Mtot + TB - 1) / TB), nk), TB, 0, h.stream>>>(es, k0, Mtot, circ.p); ::vc::note_launch();
     VC_CUDA(cudaGetLastError());
     // x: real rows -> half spectra
     {
-      int NL = smem_limit_lines<double>(g.Mx, 16);
-      int64_t nrows = (int64_t)g.My * g.Mz;
-      unsigned nblk = (unsigned)((nrows + 2 * NL - 1) / (2 * NL));
-      size_t sm = (2 * (size_t)g.Mx * NL + h.pd[0].twn) * sizeof(double2);
+      const int NL = smem_limit_lines<T>(g.Mx, 16);
+      const int64_t nrows = (int64_t)nk * g.My * g.Mz;
+      const unsigned nblk = (unsigned)((nrows + 2 * NL - 1) / (2 * NL));
+      const size_t sm = (2 * (size_t)g.Mx * NL + px.twn) * sizeof(C);
 #define VC_R2C(W)                                                                                  \
-  VC_CUDA(cudaFuncSetAttribute(k_rows_r2c<double, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)); \
-  k_rows_r2c<double, W><<<nblk, 256, sm, h.stream>>>(circ.p, nrows, g.Mx, g.Hx, spec.p, h.pd[0]);
+  VC_TRY(set_smem(k_rows_r2c<T, W>, sm));                                                          \
+  k_rows_r2c<T, W><<<nblk, 256, sm, h.stream>>>(circ.p, nrows, g.Mx, g.Hx, spec.p, px);
       VC_TILE_DISPATCH(NL, VC_R2C)
 #undef VC_R2C
       ::vc::note_launch();
       VC_CUDA(cudaGetLastError());
     }
-    // y: [Mz][My][Hx] along My
+    // y: [nk Mz][My][Hx] along My
     {
-      int TX = smem_limit_lines<double>(g.My, 16);
-      int64_t tiles = (g.Hx + TX - 1) / TX;
-      size_t sm = (2 * (size_t)g.My * TX + h.pd[1].twn) * sizeof(double2);
+      const int TX = smem_limit_lines<T>(g.My, 16);
+      const int64_t tiles = (g.Hx + TX - 1) / TX;
+      const size_t sm = (2 * (size_t)g.My * TX + py.twn) * sizeof(C);
 #define VC_C2CY(W)                                                                                  \
-  VC_CUDA(cudaFuncSetAttribute(k_strided_c2c<double, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)); \
-  k_strided_c2c<double, W><<<(unsigned)(g.Mz * tiles), 256, sm, h.stream>>>(spec.p, g.Mz, g.My, g.Hx, h.pd[1], false);
+  VC_TRY(set_smem(k_strided_c2c<T, W>, sm));                                                        \
+  k_strided_c2c<T, W><<<(unsigned)((int64_t)nk * g.Mz * tiles), 256, sm, h.stream>>>(spec.p, (int64_t)nk * g.Mz, \
+                                                                                    g.My, g.Hx, py, false);
       VC_TILE_DISPATCH(TX, VC_C2CY)
 #undef VC_C2CY
       ::vc::note_launch();
       VC_CUDA(cudaGetLastError());
     }
-    // z: [1][Mz][My*Hx] along Mz
+    // z: [nk][Mz][My*Hx] along Mz
     {
-      int TX = smem_limit_lines<double>(g.Mz, 16);
-      int64_t inner = (int64_t)g.My * g.Hx;
-      int64_t tiles = (inner + TX - 1) / TX;
-      size_t sm = (2 * (size_t)g.Mz * TX + h.pd[2].twn) * sizeof(double2);
+      const int TX = smem_limit_lines<T>(g.Mz, 16);
+      const int64_t inner = (int64_t)g.My * g.Hx;
+      const int64_t tiles = (inner + TX - 1) / TX;
+      const size_t sm = (2 * (size_t)g.Mz * TX + pz.twn) * sizeof(C);
 #define VC_C2CZ(W)                                                                                  \
-  VC_CUDA(cudaFuncSetAttribute(k_strided_c2c<double, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)); \
-  k_strided_c2c<double, W><<<(unsigned)tiles, 256, sm, h.stream>>>(spec.p, 1, g.Mz, inner, h.pd[2], false);
+  VC_TRY(set_smem(k_strided_c2c<T, W>, sm));                                                        \
+  k_strided_c2c<T, W><<<(unsigned)(nk * tiles), 256, sm, h.stream>>>(spec.p, nk, g.Mz, inner, pz, false);
       VC_TILE_DISPATCH(TX, VC_C2CZ)
 #undef VC_C2CZ
       ::vc::note_launch();
       VC_CUDA(cudaGetLastError());
     }
-    k_extract<<<(unsigned)((Otot + TB - 1) / TB), TB, 0, h.stream>>>(
-        spec.p, g, kk, kk >= 6, ker_test(kk), ker_src(kk), h.phd[0], h.phd[1], h.phd[2],
-        scale, h.spec_d.p + (size_t)kk * Otot, h.spec_f.p + (size_t)kk * Otot); ::vc::note_launch();
+    k_extract<T><<<dim3((unsigned)((Otot + TB - 1) / TB), nk), TB, 0, h.stream>>>(
+        spec.p, Htot, g, k0, h.phd[0], h.phd[1], h.phd[2], scale, h.spec_d.p, h.spec_f.p); ::vc::note_launch();
     VC_CUDA(cudaGetLastError());
   }
-  VC_CUDA(cudaStreamSynchronize(h.stream));
   return VOXCAP_OK;
 }
+
+int build_spectra(Handle& h) { return h.far32 ? spectra_impl<float>(h) : spectra_impl<double>(h); }
 
 }  // namespace vc
