@@ -2,14 +2,17 @@
 """Benchmark of the VoxCap GB300 hot path.
 
 One step = one full capacitance extraction of the workload: voxcap_setup
-from device-resident voxel labels (panels, FP64 Toeplitz tensors, circulant
-embedding and kernel spectra, preconditioner) followed by the batched
-FP32 + FP64-refinement GMRES solve of all conductors and the capacitance
+from device-resident voxel labels (panels, Toeplitz tensors -- FP64 near
+field, FP32 far-field sums under FP32+refinement --, circulant embedding and
+kernel spectra, preconditioner) followed by the batched FP32 +
+FP64-refinement GMRES solve of all conductors and the capacitance
 reduction.  ``value`` is seconds per capacitance matrix over the whole job
 (lower is better).  The same JSON line also carries the plain-FP64 time,
-the FP32 fused-product throughput (matvecs/s), the roofline of the product,
-the end-to-end number through the C ABI with host buffers, the oracle's CPU
-time on a bounded sample, clocks and the kernel-launch count.
+the FP32 fused-product throughput (matvecs/s), the HBM roofline of the
+product on the step's workload (``roofline``) and on the 128x128x64 bus
+crossing with its 8 columns (``roofline_large``), the end-to-end number
+through the C ABI with host buffers, the oracle's CPU time on a bounded
+sample, clocks and the kernel-launch count.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload plates|cube|bus|pillars]
@@ -129,6 +132,41 @@ def mvm_model_bytes(vc, nrhs):
     return 12 * vc.N + spectra / nrhs + inter
 
 
+# DRAM bytes (read + write) of one batched FP32 product, summed over its five
+# kernels, from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum`
+# (profiles/product_traffic.md); None where no capture matches the current
+# kernels.
+TRAFFIC = {"plates": None, "bus": None}
+
+
+def product_roofline(vc, dev, reps, workload_name):
+    """Time `reps` batched FP32 products (all conductor columns) with CUDA
+    events on the launching stream and relate the model bytes to the
+    measured HBM peak."""
+    import torch
+    m = vc.n_conductors
+    x = torch.randn(m, vc.N, device=dev, dtype=torch.float32)
+    for _ in range(3):
+        vc.matvec(x)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for _ in range(reps):
+        vc.matvec(x)
+    ev[1].record(stream)
+    ev[1].synchronize()
+    t = ev[0].elapsed_time(ev[1]) / 1e3 / reps
+    hbm, peak_src = read_peaks()
+    b = mvm_model_bytes(vc, m) * m
+    return m / t, {"kernel": "fused FP32 product (5 passes: xfwd, yfwd, zmac, yinv, xinv), "
+                             f"{m} columns, {workload_name}",
+                   "bound": "hbm", "achieved": b / t / 1e9, "peak": hbm, "unit": "GB/s",
+                   "frac": b / t / 1e9 / hbm, "traffic": TRAFFIC.get(workload_name),
+                   "peak_source": peak_src, "bytes_per_launch": b, "launch_s": t,
+                   "fft_lengths": list(vc.fft_lengths())}
+
+
 def run_ours(args, rank, world):
     import torch
     import __graft_entry__ as ge
@@ -204,23 +242,15 @@ def run_ours(args, rank, world):
     cerr = float(np.max(np.abs(C32 - Ct)) / np.max(np.abs(Ct)))
     # ---- fused FP32 product throughput and roofline ----
     m = vc.n_conductors
-    x = torch.randn(m, vc.N, device=dev, dtype=torch.float32)
-    for _ in range(3):
-        vc.matvec(x)
-    reps = 20
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    torch.cuda.synchronize()
-    ev[0].record(stream)
-    for _ in range(reps):
-        vc.matvec(x)
-    ev[1].record(stream)
-    ev[1].synchronize()
-    t_mvm = ev[0].elapsed_time(ev[1]) / 1e3 / reps
-    matvecs_per_s = m / t_mvm
-    hbm, peak_src = read_peaks()
-    bytes_per = mvm_model_bytes(vc, m) * m
-    achieved = bytes_per / t_mvm / 1e9
+    matvecs_per_s, roof = product_roofline(vc, dev, 20, args.workload)
     vc.close()
+    # ---- the product on the bus crossing (8 columns, 110,848 panels) ----
+    roof_large = None
+    if args.workload != "bus":
+        wb, _ = workload("bus")
+        vb = V.VoxCap(torch.tensor(wb.labels, device=dev), wb.conductor_id, wb.eps_r, wb.voxel_size)
+        _, roof_large = product_roofline(vb, dev, 10, "bus")
+        vb.close()
     # ---- end to end through the C ABI with host buffers ----
     e2e = []
     lab_host = np.ascontiguousarray(w.labels, dtype=np.int32)
@@ -254,11 +284,8 @@ def run_ours(args, rank, world):
         "fp64": {"s_per_C": sum(t64) / len(t64), "iterations": st64["iterations"],
                  "products": st64["matvecs"]},
         "matvecs_per_s": matvecs_per_s,
-        "roofline": {"kernel": "fused FP32 product (5 passes)", "bound": "hbm",
-                     "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None,
-                     "peak_source": peak_src, "bytes_per_launch": bytes_per,
-                     "launch_s": t_mvm},
+        "roofline": roof,
+        "roofline_large": roof_large,
         "e2e": {"value": statistics.median(e2e), "unit": "s/C-matrix", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),

@@ -94,6 +94,43 @@ struct Panels {
   DBuf<int32_t> struct_of;        // [N] structure of each panel
 };
 
+// Pinned host ints the device writes directly (mapped), e.g. the per-step
+// active flags of GMRES that the host polls.
+struct HostMap {
+  int* h = nullptr;
+  int* d = nullptr;
+  size_t n = 0;
+  int ensure(size_t count) {
+    if (count <= n && h) return VOXCAP_OK;
+    release();
+    if (cudaHostAlloc(reinterpret_cast<void**>(&h), count * sizeof(int), cudaHostAllocMapped) != cudaSuccess) {
+      h = nullptr;
+      (void)cudaGetLastError();
+      set_error("mapped host allocation failed");
+      return VOXCAP_ERR_OOM;
+    }
+    if (cudaHostGetDevicePointer(reinterpret_cast<void**>(&d), h, 0) != cudaSuccess) {
+      (void)cudaGetLastError();
+      release();
+      set_error("mapped host pointer unavailable");
+      return VOXCAP_ERR_CUDA;
+    }
+    n = count;
+    for (size_t i = 0; i < n; ++i) h[i] = 0;
+    return VOXCAP_OK;
+  }
+  void release() {
+    if (h) cudaFreeHost(h);
+    h = nullptr;
+    d = nullptr;
+    n = 0;
+  }
+  ~HostMap() { release(); }
+  HostMap() = default;
+  HostMap(const HostMap&) = delete;
+  HostMap& operator=(const HostMap&) = delete;
+};
+
 struct Precond {
   int kind = VOXCAP_PRECOND_BDD;
   int nv[3] = {10, 10, 10};
@@ -154,6 +191,7 @@ struct Handle {
   DBuf<double> rhs;               // last capacitance RHS
   bool have_rho = false;
   DBuf<char> solver_ws;
+  HostMap act_map;                // GMRES: active flags per step parity, [2][nrhs]
 };
 
 // ---- per-precision views of the handle's plans, phases and spectra

@@ -279,148 +279,184 @@ __global__ void k_assemble(ToepTabs tt, const int32_t* urep, const int32_t* offs
   }
 }
 
-// Inverse of one unique block of n <= 32 RA panels held in registers by
-// one CTA of 16 warps (FP32; the preconditioner only steers GMRES, the
-// solution's accuracy comes from the residuals).  Thread (warp w, lane l)
-// holds rows i = l + 32 a and columns j = w + 16 b.  In-place Gauss-Jordan
+// Inverse of one unique block of n <= 224 panels, held in shared memory by
+// one CTA of 32 warps (FP32; the preconditioner only steers GMRES, the
+// solution's accuracy comes from the residuals).  In-place Gauss-Jordan
 // with pivot bookkeeping: step k takes as pivot the unused row p_k with the
 // largest |S[p][k]|, scales that row and eliminates column k from every
 // other row; column k, now a unit vector, stores column p_k of the
-// inverse-to-be, and A^-1[q_i][p_j] = S[i][j] at the end (q = p^-1).  The
-// warp owning column k finds the pivot from its own registers and publishes
-// the column through shared memory (double-buffered by step parity), row p
-// reaches the other lanes of each warp by shuffles: one barrier per step.
+// inverse-to-be, and A^-1[q_i][p_j] = S[i][j] at the end (q = p^-1).
+// Blocked by panels K of 16 columns: the steps of a panel touch only its
+// columns (warp c < 16 owns panel column c, so the owner of the next column
+// finds its pivot without a barrier; one barrier per step publishes the
+// pivot column), then the panel's transformation T_K x = x (rows P_K zeroed)
+// + S[:, K] x[P_K] is applied to every other column as one rank-16 update
+// by all 32 warps.
 constexpr int kGJTileMax = 224;
-constexpr int kGJWarps = 16;
+constexpr int kGJPanel = 16;                     // = warps per CTA
 
-template <int RA>
-__global__ void __launch_bounds__(32 * kGJWarps, 1)
+__global__ void __launch_bounds__(1024, 1)
 k_block_inverse(ToepTabs tt, const int32_t* __restrict__ urep, const int32_t* __restrict__ offs,
                 const int32_t* __restrict__ idx, const int64_t* __restrict__ uoff,
                 const int8_t* __restrict__ orient, const int32_t* __restrict__ face,
                 const int8_t* __restrict__ kind, const double* __restrict__ idiag,
                 double* __restrict__ inv_d, float* __restrict__ inv_f, int* __restrict__ status) {
-  constexpr int CB = 2 * RA;
-  constexpr int NMAX = 32 * RA;
-  __shared__ float colb[2][NMAX];
+  extern __shared__ float gj_sm[];
+  __shared__ float colb[2][kGJTileMax];
+  __shared__ int perm[kGJTileMax], qinv[kGJTileMax];
+  __shared__ unsigned char used[kGJTileMax];
   __shared__ int prow[2];
   __shared__ float pinv[2];
-  __shared__ int perm[NMAX], qinv[NMAX];
+  __shared__ int pan_rows[kGJPanel];
   __shared__ int fail;
   const int u = blockIdx.x;
   const int gb = urep[u];
   const int q0 = offs[gb];
   const int n = offs[gb + 1] - q0;
-  if (n > NMAX || n == 0) return;                    // larger blocks take the multi-CTA path
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  float S[RA][CB];
-#pragma unroll
-  for (int a = 0; a < RA; ++a) {
-    const int i = lane + 32 * a;
-    int ck[3] = {0, 0, 0}, pk = 0;
-    if (i < n) {
-      pk = idx[q0 + i];
-      face_coords(tt.n, orient[pk], face[pk], ck);
-    }
-#pragma unroll
-    for (int b = 0; b < CB; ++b) {
-      const int j = w + kGJWarps * b;
-      float v = 0.0f;
-      if (i < n && j < n) {
-        const int pl = idx[q0 + j];
-        int cl[3];
-        face_coords(tt.n, orient[pl], face[pl], cl);
-        const bool E = kind[pk] == 1;
-        double e = a_entry(tt, E, orient[pk], ck, orient[pl], cl);
-        if (E && i == j) e += idiag[pk];
-        v = (float)e;
-      }
-      S[a][b] = v;
-    }
+  if (n > kGJTileMax || n == 0) return;              // larger blocks take the multi-CTA path
+  const int ld = n | 1;
+  float* S = gj_sm;                                  // [n][ld]
+  float* Bp = gj_sm + (size_t)n * ld;                // [kGJPanel][ld]: rows P_K before the update
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, w = tid >> 5;
+  // per-panel face coordinates and kinds, once
+  int* pc = reinterpret_cast<int*>(Bp);              // [4][n] (Bp is free until the first panel)
+  for (int i = tid; i < n; i += nt) {
+    const int pk = idx[q0 + i];
+    int c[3];
+    face_coords(tt.n, orient[pk], face[pk], c);
+    pc[i] = c[0];
+    pc[n + i] = c[1];
+    pc[2 * n + i] = c[2];
+    pc[3 * n + i] = orient[pk] | (kind[pk] << 2);
   }
-  if (threadIdx.x == 0) fail = 0;
-  unsigned used = 0;                                 // bit a: row lane + 32 a already a pivot
-  for (int k = 0; k < n; ++k) {
-    const int par = k & 1;
-    if (w == k % kGJWarps) {                         // pivot search in the owner of column k
-      const int bk = k / kGJWarps;
-      float best = -1.0f;
-      int bi = n;
-#pragma unroll
-      for (int a = 0; a < RA; ++a) {
-        const int i = lane + 32 * a;
-        float v = 0.0f;
-#pragma unroll
-        for (int b = 0; b < CB; ++b)
-          if (b == bk) v = S[a][b];
-        if (i < n) {
+  __syncthreads();
+  for (int t = tid; t < n * n; t += nt) {
+    const int i = t / n, j = t - (t / n) * n;
+    const int ck[3] = {pc[i], pc[n + i], pc[2 * n + i]};
+    const int cl[3] = {pc[j], pc[n + j], pc[2 * n + j]};
+    const int oi = pc[3 * n + i] & 3, oj = pc[3 * n + j] & 3;
+    const bool E = (pc[3 * n + i] >> 2) == 1;
+    double v = a_entry(tt, E, oi, ck, oj, cl);
+    if (E && i == j) v += idiag[idx[q0 + i]];
+    S[i * ld + j] = (float)v;
+  }
+  for (int i = tid; i < n; i += nt) used[i] = 0;
+  if (tid == 0) fail = 0;
+  __syncthreads();
+  for (int k0 = 0; k0 < n && !fail; k0 += kGJPanel) {
+    const int nbp = min(kGJPanel, n - k0);
+    for (int kk = 0; kk < nbp; ++kk) {
+      const int k = k0 + kk, par = k & 1;
+      if (w == kk) {                                 // pivot search by the owner of column k
+        float best = -1.0f;
+        int bi = n;
+        for (int i = lane; i < n; i += 32) {
+          const float v = S[i * ld + k];
           colb[par][i] = v;
-          if (!((used >> a) & 1u) && fabsf(v) > best) { best = fabsf(v); bi = i; }
+          if (!used[i] && fabsf(v) > best) { best = fabsf(v); bi = i; }
+        }
+        for (int d = 16; d > 0; d >>= 1) {
+          const float ob = __shfl_down_sync(0xffffffffu, best, d);
+          const int oi = __shfl_down_sync(0xffffffffu, bi, d);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        __syncwarp();
+        if (lane == 0) {
+          if (!(best > 0.0f) || bi >= n) {
+            fail = 1;
+            bi = 0;
+          }
+          prow[par] = bi;
+          pinv[par] = 1.0f / colb[par][bi];
+          perm[k] = bi;
+          used[bi] = 1;
+          pan_rows[kk] = bi;
         }
       }
-      for (int d = 16; d > 0; d >>= 1) {
-        const float ob = __shfl_down_sync(0xffffffffu, best, d);
-        const int oi = __shfl_down_sync(0xffffffffu, bi, d);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-      }
-      __syncwarp();
-      if (lane == 0) {
-        if (!(best > 0.0f) || bi >= n) {
-          fail = 1;
-          bi = 0;
+      __syncthreads();
+      if (fail) break;                               // uniform: read after the barrier
+      const int p = prow[par];
+      const float ip = pinv[par];
+      if (w < nbp) {                                 // warp w updates panel column k0 + w
+        const int c = k0 + w;
+        const float sp = S[p * ld + c];
+        __syncwarp();                                // every lane has row p's old value
+        const float rpc = (c == k ? 1.0f : sp) * ip;
+        for (int i = lane; i < n; i += 32) {
+          float* e = S + i * ld + c;
+          if (i == p) *e = rpc;
+          else *e = (c == k ? 0.0f : *e) - colb[par][i] * rpc;
         }
-        prow[par] = bi;
-        pinv[par] = 1.0f / colb[par][bi];
-        perm[k] = bi;
       }
     }
     __syncthreads();
-    if (fail) break;                                 // uniform: read after the barrier
-    const int p = prow[par];
-    const float ip = pinv[par];
-    const int lp = p & 31, ap = p >> 5;
-    if (lane == lp) used |= 1u << ap;
-    float rp[CB];                                    // row p, scaled, in this thread's columns
-#pragma unroll
-    for (int b = 0; b < CB; ++b) {
-      float v = 0.0f;
-#pragma unroll
-      for (int a = 0; a < RA; ++a)
-        if (a == ap) v = S[a][b];
-      v = __shfl_sync(0xffffffffu, v, lp);
-      rp[b] = ((w + kGJWarps * b) == k ? 1.0f : v) * ip;
+    if (fail) break;
+    // rank-nbp update of the columns outside the panel
+    for (int t = tid; t < nbp * n; t += nt) {
+      const int r = t / n, j = t - (t / n) * n;
+      Bp[r * ld + j] = S[pan_rows[r] * ld + j];
     }
+    __syncthreads();
+    const int nwarps = nt >> 5;
+    for (int i0 = 4 * w; i0 < n; i0 += 4 * nwarps) {
+      float acc[4][8];
 #pragma unroll
-    for (int a = 0; a < RA; ++a) {
-      const int i = lane + 32 * a;
-      const float f = i < n ? colb[par][i] : 0.0f;
+      for (int q = 0; q < 4; ++q)
 #pragma unroll
-      for (int b = 0; b < CB; ++b) {
-        const int j = w + kGJWarps * b;
-        if (i == p) S[a][b] = rp[b];
-        else S[a][b] = (j == k ? 0.0f : S[a][b]) - f * rp[b];
+        for (int e = 0; e < 8; ++e) acc[q][e] = 0.0f;
+      auto rank1 = [&](int r) {
+        float av[4], bv[8];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) av[q] = (i0 + q < n) ? S[(i0 + q) * ld + k0 + r] : 0.0f;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int j = lane + 32 * e;
+          bv[e] = j < n ? Bp[r * ld + j] : 0.0f;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int e = 0; e < 8; ++e) acc[q][e] += av[q] * bv[e];
+      };
+      if (nbp == kGJPanel) {
+#pragma unroll
+        for (int r = 0; r < kGJPanel; ++r) rank1(r);
+      } else {
+        for (int r = 0; r < nbp; ++r) rank1(r);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = i0 + q;
+        if (i >= n) continue;
+        bool in_pan = false;
+        for (int r = 0; r < nbp; ++r) in_pan = in_pan || pan_rows[r] == i;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int j = lane + 32 * e;
+          if (j < n && (j < k0 || j >= k0 + nbp)) {
+            float* x = S + i * ld + j;
+            *x = (in_pan ? 0.0f : *x) + acc[q][e];
+          }
+        }
       }
     }
+    __syncthreads();
   }
-  __syncthreads();
   if (fail) {
-    if (threadIdx.x == 0) atomicExch(status, 1);
+    if (tid == 0) atomicExch(status, 1);
     return;
   }
-  for (int k = threadIdx.x; k < n; k += blockDim.x) qinv[perm[k]] = k;
+  for (int k = tid; k < n; k += nt) qinv[perm[k]] = k;
   __syncthreads();
   const int64_t o = uoff[u];
-#pragma unroll
-  for (int a = 0; a < RA; ++a)
-#pragma unroll
-    for (int b = 0; b < CB; ++b) {
-      const int i = lane + 32 * a, j = w + kGJWarps * b;
-      if (i < n && j < n) {
-        const int64_t t = o + (int64_t)qinv[i] * n + perm[j];
-        inv_f[t] = S[a][b];
-        inv_d[t] = (double)S[a][b];
-      }
-    }
+  for (int t = tid; t < n * n; t += nt) {
+    const int i = t / n, j = t - (t / n) * n;
+    const float v = S[i * ld + j];
+    const int64_t d = o + (int64_t)qinv[i] * n + perm[j];
+    inv_f[d] = v;
+    inv_d[d] = (double)v;
+  }
 }
 
 // Gauss-Jordan with partial pivoting on [A | I] -> [I | A^-1], one launch
@@ -651,20 +687,12 @@ int build_precond(Handle& h) {
   }
   tt.n[0] = g.nx; tt.n[1] = g.ny; tt.n[2] = g.nz;
   if (max_small > 0) {
-    // blocks of up to kGJTileMax panels: one CTA each, the block in registers
-    const int RA = (max_small + 31) / 32;
-#define VC_BINV(R)                                                                                  \
-  case R:                                                                                           \
-    k_block_inverse<R><<<(unsigned)nuniq, 32 * kGJWarps, 0, h.stream>>>(                            \
-        tt, urep.p, P.blk_off.p, P.blk_idx.p, P.uoff.p, h.pan.orient.p, h.pan.face.p, h.pan.kind.p,  \
-        h.pan.idiag.p, P.inv_d.p, P.inv_f.p, status.p);                                             \
-    break;
-    switch (RA) {
-      VC_BINV(1) VC_BINV(2) VC_BINV(3) VC_BINV(4) VC_BINV(5) VC_BINV(6) VC_BINV(7)
-      default: VC_CHECK(false, VOXCAP_ERR_UNSUPPORTED, "block too large for the register inverse");
-    }
-#undef VC_BINV
-    ::vc::note_launch();
+    // blocks of up to kGJTileMax panels: one CTA each, the block in shared memory
+    const size_t sm = sizeof(float) * (size_t)(max_small + kGJPanel) * (max_small | 1);
+    VC_CUDA(cudaFuncSetAttribute(k_block_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_block_inverse<<<(unsigned)nuniq, 1024, sm, h.stream>>>(
+        tt, urep.p, P.blk_off.p, P.blk_idx.p, P.uoff.p, h.pan.orient.p, h.pan.face.p, h.pan.kind.p,
+        h.pan.idiag.p, P.inv_d.p, P.inv_f.p, status.p); ::vc::note_launch();
     VC_CUDA(cudaGetLastError());
   }
   if (nlarge > 0) {

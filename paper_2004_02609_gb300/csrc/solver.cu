@@ -245,59 +245,9 @@ static int nchunks_for(int64_t N, int nrhs) {
 }
 
 // ---- kernels of the graph-captured Arnoldi step (iteration index on the device) ----
-// One CGS pass over the basis V[0..j] (j = *jdev): optionally w -= sum_i coef_i V_i,
-// then partial dots with V_i (dot) or ||w||^2 (norm).
-template <typename T>
-__global__ void k_gs_dev(const T* __restrict__ V, T* __restrict__ w, int64_t N, int nrhs, bool update,
-                         const double* __restrict__ coef, int coef_ld, bool dot, const int* __restrict__ jdev,
-                         const int* __restrict__ active, int nchunks, double* __restrict__ partial, int part_ld) {
-  const int col = blockIdx.y;
-  const int chunk = blockIdx.x;
-  if (!active[col]) return;
-  const int nv = *jdev + 1;
-  const int64_t per = (N + nchunks - 1) / nchunks;
-  const int64_t lo = chunk * per, hi = min(N, lo + per);
-  T* wc = w + (int64_t)col * N;
-  const int64_t vstride = (int64_t)nrhs * N;
-  if (update) {
-    for (int64_t p = lo + threadIdx.x; p < hi; p += blockDim.x) {
-      double acc = (double)wc[p];
-      for (int i = 0; i < nv; ++i)
-        acc -= coef[(int64_t)col * coef_ld + i] * (double)V[i * vstride + (int64_t)col * N + p];
-      wc[p] = (T)acc;
-    }
-    __syncthreads();
-  }
-  const int nd = dot ? nv : 1;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = wid; i < nd; i += nw) {
-    const T* vi = dot ? V + i * vstride + (int64_t)col * N : wc;
-    double acc = 0.0;
-    for (int64_t p = lo + lane; p < hi; p += 32) acc += (double)vi[p] * (double)wc[p];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0) partial[((int64_t)col * part_ld + i) * nchunks + chunk] = acc;
-  }
-}
-
-// out[col][i] = sum_chunk partial[col][i][chunk], i < (*jdev + 1) (dot) or i = 0 (norm)
-__global__ void k_reduce_dev(const double* __restrict__ partial, int nchunks, bool dot, const int* __restrict__ jdev,
-                             int part_ld, const int* __restrict__ active, double* __restrict__ out, int out_ld) {
-  __shared__ double sh[32];
-  const int col = blockIdx.y, i = blockIdx.x;
-  if (!active[col]) return;
-  if (i >= (dot ? *jdev + 1 : 1)) return;
-  double acc = 0.0;
-  for (int c = threadIdx.x; c < nchunks; c += blockDim.x) acc += partial[((int64_t)col * part_ld + i) * nchunks + c];
-  double s = block_sum(acc, sh);
-  if (threadIdx.x == 0) out[(int64_t)col * out_ld + i] = s;
-}
-
-__global__ void k_givens_dev(GState s, int nrhs, int m, const int* __restrict__ jdev, double rtol, int max_it,
-                             double* inv_norm) {
-  const int col = blockIdx.x * blockDim.x + threadIdx.x;
-  if (col >= nrhs) return;
-  const int j = *jdev;
-  if (!s.active[col] || j >= m) { inv_norm[col] = 0.0; return; }
+// After the two Gram-Schmidt passes: H[:,j] = hcol + hcol2, h_{j+1,j} = sqrt(nrm2);
+// Givens update; convergence test; scale factor for the new basis vector.
+__device__ void givens_col(GState s, int col, int m, int j, double rtol, int max_it, double* inv_norm) {
   double* H = s.H + (int64_t)col * (m + 1) * m + (int64_t)j * (m + 1);
   double* cs = s.cs + (int64_t)col * m;
   double* sn = s.sn + (int64_t)col * m;
@@ -326,25 +276,103 @@ __global__ void k_givens_dev(GState s, int nrhs, int m, const int* __restrict__ 
   inv_norm[col] = hn > 0.0 ? 1.0 / hn : 0.0;
 }
 
-// V[j+1] = w * invn and vcur = V[j+1] for the columns still iterating; then j += 1
+// True for the one CTA that finishes last among `count` (a fenced ticket; no
+// CTA waits).  That CTA resets the ticket for the next use.
+__device__ __forceinline__ bool last_cta(unsigned* ticket, unsigned count) {
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    is_last = atomicAdd(ticket, 1u) == count - 1;
+    if (is_last) *ticket = 0;
+  }
+  __syncthreads();
+  if (is_last) __threadfence();
+  return is_last;
+}
+
+struct StepArgs {
+  int64_t N;
+  int nrhs, m, nchunks, part_ld;
+  double rtol;
+  int max_it;
+  int* jdev;
+  double* partial;
+  unsigned* tickets;     // [nrhs] per-column tickets
+  double* invn;
+};
+
+// One CGS pass of step j = *jdev over V[0..j] for column blockIdx.y, chunk
+// blockIdx.x: pass 0: dots V_i . w -> hcol; pass 1: w -= sum hcol_i V_i, dots
+// -> hcol2; pass 2: w -= sum hcol2_i V_i, ||w||^2 -> nrm2, then the Givens
+// update of the column.  The last CTA of a column sums its partials.
 template <typename T>
-__global__ void k_store_next(const T* __restrict__ w, T* __restrict__ V, T* __restrict__ vcur, int64_t N, int nrhs,
-                             const int* __restrict__ jdev, int m, const double* __restrict__ invn,
-                             const int* __restrict__ kused, int* __restrict__ jnext) {
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_gs_step(const T* __restrict__ V, T* __restrict__ w, int pass, GState s, StepArgs a) {
+  __shared__ double sh[32];
+  const int col = blockIdx.y;
+  const int chunk = blockIdx.x;
+  if (!s.active[col]) return;                        // whole column: no CTA takes a ticket
+  const int j = *a.jdev;
+  const int nv = j + 1;
+  const int64_t N = a.N;
+  const int64_t per = (N + a.nchunks - 1) / a.nchunks;
+  const int64_t lo = chunk * per, hi = min(N, lo + per);
+  T* wc = w + (int64_t)col * N;
+  const int64_t vstride = (int64_t)a.nrhs * N;
+  if (pass > 0) {
+    const double* coef = (pass == 1 ? s.hcol : s.hcol2) + (int64_t)col * (a.m + 1);
+    for (int64_t p = lo + threadIdx.x; p < hi; p += blockDim.x) {
+      double acc = (double)wc[p];
+      for (int i = 0; i < nv; ++i) acc -= coef[i] * (double)V[i * vstride + (int64_t)col * N + p];
+      wc[p] = (T)acc;
+    }
+    __syncthreads();
+  }
+  const bool dot = pass < 2;
+  const int nd = dot ? nv : 1;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = wid; i < nd; i += nw) {
+    const T* vi = dot ? V + i * vstride + (int64_t)col * N : wc;
+    double acc = 0.0;
+    for (int64_t p = lo + lane; p < hi; p += 32) acc += (double)vi[p] * (double)wc[p];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) a.partial[((int64_t)col * a.part_ld + i) * a.nchunks + chunk] = acc;
+  }
+  if (!last_cta(a.tickets + col, (unsigned)a.nchunks)) return;
+  double* out = pass == 0 ? s.hcol + (int64_t)col * (a.m + 1)
+              : pass == 1 ? s.hcol2 + (int64_t)col * (a.m + 1) : s.nrm2 + col;
+  for (int i = 0; i < nd; ++i) {
+    double acc = 0.0;
+    for (int c = threadIdx.x; c < a.nchunks; c += blockDim.x)
+      acc += __ldcg(a.partial + ((int64_t)col * a.part_ld + i) * a.nchunks + c);
+    const double t = block_sum(acc, sh);
+    if (threadIdx.x == 0) out[i] = t;
+  }
+  if (pass == 2 && threadIdx.x == 0 && j < a.m) givens_col(s, col, a.m, j, a.rtol, a.max_it, a.invn);
+}
+
+// V[j+1] = w * invn and vcur = V[j+1] for the columns that took step j; the
+// columns' active flags to the host-mapped slot of step j's parity; the last
+// CTA advances *jdev.
+template <typename T>
+__global__ void k_store_next(const T* __restrict__ w, T* __restrict__ V, T* __restrict__ vcur, GState s,
+                             StepArgs a, unsigned* __restrict__ ticket, int* __restrict__ act_map) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int* jdev = a.jdev;
   const int j = *jdev;
-  if (t < N * nrhs && j < m) {
+  const int64_t N = a.N;
+  if (t < N * a.nrhs && j < a.m) {
     const int col = (int)(t / N);
-    if (kused[col] == j + 1) {          // this column took step j
-      const T v = (T)((double)w[t] * invn[col]);
-      V[(int64_t)(j + 1) * N * nrhs + t] = v;
+    if (s.kused[col] == j + 1) {          // this column took step j
+      const T v = (T)((double)w[t] * a.invn[col]);
+      V[(int64_t)(j + 1) * N * a.nrhs + t] = v;
       vcur[t] = v;
     }
   }
-  if (t == 0) *jnext = j + 1;
+  if (blockIdx.x == 0)
+    for (int c = threadIdx.x; c < a.nrhs; c += blockDim.x) act_map[(j & 1) * a.nrhs + c] = s.active[c];
+  if (last_cta(ticket, gridDim.x) && threadIdx.x == 0) *jdev = j + 1;
 }
-
-__global__ void k_copy_j(const int* __restrict__ src, int* __restrict__ dst) { *dst = *src; }
 
 // Solve R A d = R r (x0 = 0) per column to a preconditioned relative
 // residual rtol.  r, d: device [nrhs][N] in T.  `adjoint`: use A^T.
@@ -364,7 +392,7 @@ static int gmres(Handle& h, const T* r, T* d, int nrhs, double rtol, int max_it,
   size_t bytes = sizeof(T) * (nV + 3 * nW) + 256;
   const size_t nd_H = (size_t)nrhs * (m + 1) * m, nd_cs = (size_t)nrhs * m, nd_g = (size_t)nrhs * (m + 1);
   const size_t ndbl = nd_H + 2 * nd_cs + 3 * nd_g + 3 * (size_t)nrhs + (size_t)nrhs * (m + 1) * nch;
-  bytes += sizeof(double) * ndbl + sizeof(int) * (3 * nrhs + 4) + 256;
+  bytes += sizeof(double) * ndbl + sizeof(int) * (3 * nrhs + 4) + sizeof(unsigned) * (nrhs + 1) + 256;
   VC_TRY(h.solver_ws.alloc(bytes));
   char* wp = h.solver_ws.p;
   T* V = reinterpret_cast<T*>(wp); wp += sizeof(T) * nV;
@@ -389,8 +417,10 @@ static int gmres(Handle& h, const T* r, T* d, int nrhs, double rtol, int max_it,
   s.kused = ip; ip += nrhs;
   s.iters = ip; ip += nrhs;
   int* jdev = ip; ip += 1;
-  int* jnext = ip; ip += 1;
+  unsigned* tickets = reinterpret_cast<unsigned*>(ip + 1);    // [nrhs] columns, [nrhs] the store
   VC_CUDA(cudaMemsetAsync(d, 0, sizeof(T) * nW, st));
+  VC_CUDA(cudaMemsetAsync(tickets, 0, sizeof(unsigned) * (nrhs + 1), st));
+  VC_TRY(h.act_map.ensure((size_t)2 * nrhs));
   const int TB = 256;
   const unsigned gN = (unsigned)((N * nrhs + TB - 1) / TB);
   const unsigned gC = (unsigned)((nrhs + 63) / 64);
@@ -412,16 +442,15 @@ static int gmres(Handle& h, const T* r, T* d, int nrhs, double rtol, int max_it,
     if (rc == VOXCAP_OK) rc = mvm<T>(h, vcur, W, nrhs, adjoint, nullptr);
     if (rc == VOXCAP_OK) rc = precond_apply<T>(h, W, W2, nrhs);
     if (rc == VOXCAP_OK) {
-      dim3 gsw(nch, nrhs), grd(m + 1, nrhs);
-      k_gs_dev<T><<<gsw, kDotTB, 0, cap>>>(V, W2, N, nrhs, false, nullptr, 0, true, jdev, s.active, nch, partial, m + 1);
-      k_reduce_dev<<<grd, kDotTB, 0, cap>>>(partial, nch, true, jdev, m + 1, s.active, s.hcol, m + 1);
-      k_gs_dev<T><<<gsw, kDotTB, 0, cap>>>(V, W2, N, nrhs, true, s.hcol, m + 1, true, jdev, s.active, nch, partial, m + 1);
-      k_reduce_dev<<<grd, kDotTB, 0, cap>>>(partial, nch, true, jdev, m + 1, s.active, s.hcol2, m + 1);
-      k_gs_dev<T><<<gsw, kDotTB, 0, cap>>>(V, W2, N, nrhs, true, s.hcol2, m + 1, false, jdev, s.active, nch, partial, m + 1);
-      k_reduce_dev<<<dim3(1, nrhs), kDotTB, 0, cap>>>(partial, nch, false, jdev, m + 1, s.active, s.nrm2, 1);
-      k_givens_dev<<<gC, 64, 0, cap>>>(s, nrhs, m, jdev, rtol, max_it, invn);
-      k_store_next<T><<<gN, TB, 0, cap>>>(W2, V, vcur, N, nrhs, jdev, m, invn, s.kused, jnext);
-      k_copy_j<<<1, 1, 0, cap>>>(jnext, jdev);
+      dim3 gsw(nch, nrhs);
+      StepArgs sa;
+      sa.N = N; sa.nrhs = nrhs; sa.m = m; sa.nchunks = nch; sa.part_ld = m + 1;
+      sa.rtol = rtol; sa.max_it = max_it; sa.jdev = jdev; sa.partial = partial;
+      sa.tickets = tickets; sa.invn = invn;
+      k_gs_step<T><<<gsw, kDotTB, 0, cap>>>(V, W2, 0, s, sa);
+      k_gs_step<T><<<gsw, kDotTB, 0, cap>>>(V, W2, 1, s, sa);
+      k_gs_step<T><<<gsw, kDotTB, 0, cap>>>(V, W2, 2, s, sa);
+      k_store_next<T><<<gN, TB, 0, cap>>>(W2, V, vcur, s, sa, tickets + nrhs, h.act_map.d);
     }
     cudaError_t ce = cudaStreamEndCapture(cap, &graph);
     h.stream = saved;
@@ -443,14 +472,8 @@ static int gmres(Handle& h, const T* r, T* d, int nrhs, double rtol, int max_it,
   } guard{exec};
   // kernel launches inside one step (counted per replay)
   const int step_launches = 5 + ((h.pre.kind == VOXCAP_PRECOND_BDD || h.pre.kind == VOXCAP_PRECOND_BD) &&
-                                 h.pre.nblocks > 0 && h.pre.max_n > 0 ? 2 : 1) + 9;
+                                 h.pre.nblocks > 0 && h.pre.max_n > 0 ? 2 : 1) + 4;
 
-  int* act_h = nullptr;
-  VC_CUDA(cudaMallocHost(&act_h, sizeof(int) * 2 * nrhs));
-  struct HostGuard {
-    int* p;
-    ~HostGuard() { if (p) cudaFreeHost(p); }
-  } hguard{act_h};
   cudaEvent_t ev[2];
   VC_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
   VC_CUDA(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
@@ -488,8 +511,6 @@ static int gmres(Handle& h, const T* r, T* d, int nrhs, double rtol, int max_it,
       VC_CUDA(cudaGraphLaunch(exec, st));
       for (int q = 0; q < step_launches; ++q) ::vc::note_launch();
       cnt->matvecs += 1;
-      VC_CUDA(cudaMemcpyAsync(act_h + (launched & 1) * nrhs, s.active, sizeof(int) * nrhs,
-                              cudaMemcpyDeviceToHost, st));
       VC_CUDA(cudaEventRecord(ev[launched & 1], st));
       ++launched;
       return VOXCAP_OK;
@@ -498,7 +519,7 @@ static int gmres(Handle& h, const T* r, T* d, int nrhs, double rtol, int max_it,
     while (!done) {
       if (launched < m) VC_TRY(launch_step());
       VC_CUDA(cudaEventSynchronize(ev[checked & 1]));
-      const int* a = act_h + (checked & 1) * nrhs;
+      const volatile int* a = h.act_map.h + (checked & 1) * nrhs;   // written by step `checked`
       ++checked;
       bool any = false;
       for (int c = 0; c < nrhs; ++c) any = any || a[c];

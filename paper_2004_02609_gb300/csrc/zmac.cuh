@@ -80,9 +80,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_zmac(Geom g, C_
   C* twv = twf + pf.twn;
   load_twiddles(twf, pf);
   load_twiddles(twv, pv);
-  const int b = blockIdx.y;
+  const int b = blockIdx.x;                             // batch items of one tile run together
   const int64_t zstride = (int64_t)g.My * H;            // one z plane: [My][H], contiguous
-  const int q0 = blockIdx.x * TX;                       // first (ky, kx) column: q = ky * H + kx
+  const int q0 = blockIdx.y * TX;                       // first (ky, kx) column: q = ky * H + kx
   const int64_t gstride = (int64_t)g.Lz * zstride;      // one grid of one batch item
   C* base = data + (int64_t)b * 6 * gstride + q0;
   const int ncol = (int)min((int64_t)TX, zstride - q0); // valid columns of this tile
@@ -148,16 +148,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_zmac(Geom g, C_
   const int kx = q - ky * H;
   const bool fy = ky > g.My / 2;
   const int kyf = fy ? g.My - ky : ky;
-  int sidx[RL];
-  uint32_t sneg[RL];
-#pragma unroll
-  for (int r = 0; r < RL; ++r) {
+  // spectral index and fold-sign mask of frequency kz = j + r nb (recomputed
+  // where used: a few integer operations, no registers held across the MAC)
+  const uint32_t negy = fy ? neg_y : 0u;
+  const int kcol = kyf * H + kx;
+  auto sidx = [&](int r) -> int {
     const int kz = j + r * nb;
-    const bool fz = kz > M / 2;
-    sneg[r] = (fy ? neg_y : 0u) ^ (fz ? neg_z : 0u);
-    const int kzf = fz ? M - kz : kz;
-    sidx[r] = (kzf * g.Oy + kyf) * H + kx;
-  }
+    return ((kz > M / 2 ? M - kz : kz) * g.Oy) * H + kcol;
+  };
+  auto sneg = [&](int r) -> uint32_t { return negy ^ ((j + r * nb) > M / 2 ? neg_z : 0u); };
   auto put = [&](int grid, C* o) {                      // inverse first stage (Ns = 1) and store
     if (grid % 3 == 2) {
 #pragma unroll
@@ -187,7 +186,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_zmac(Geom g, C_
           if (col_ok) {
 #pragma unroll
             for (int be = 0; be < 3; ++be)
-              acc = cadd(acc, cscale(in[be][r], spec_at(spec, Otot, pidx(al, be), sidx[r], sneg[r])));
+              acc = cadd(acc, cscale(in[be][r], spec_at(spec, Otot, pidx(al, be), sidx(r), sneg(r))));
           }
           o[r] = acc;
         }
@@ -198,7 +197,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_zmac(Geom g, C_
           if (col_ok) {
 #pragma unroll
             for (int be = 0; be < 3; ++be)
-              acc = cadd(acc, cscale(in[be][r], spec_at(spec, Otot, eidx(al, be), sidx[r], sneg[r])));
+              acc = cadd(acc, cscale(in[be][r], spec_at(spec, Otot, eidx(al, be), sidx(r), sneg(r))));
           }
           o[r] = cmul_mi(acc);
         }
@@ -223,9 +222,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_zmac(Geom g, C_
 #pragma unroll
           for (int r = 0; r < RL; ++r) {
             if (gi < 3) {
-              o[be][r] = cadd(o[be][r], cscale(v[r], spec_at(spec, Otot, pidx(al, be), sidx[r], sneg[r])));
+              o[be][r] = cadd(o[be][r], cscale(v[r], spec_at(spec, Otot, pidx(al, be), sidx(r), sneg(r))));
             } else {
-              o[be][r] = cadd(o[be][r], cmul_pi(cscale(v[r], spec_at(spec, Otot, eidx(al, be), sidx[r], sneg[r]))));
+              o[be][r] = cadd(o[be][r], cmul_pi(cscale(v[r], spec_at(spec, Otot, eidx(al, be), sidx(r), sneg(r)))));
             }
           }
       }
@@ -274,9 +273,9 @@ int zmac_launch(const Handle& h, C_t<T>* data, int B, cudaStream_t st) {
     if (fold_sign(kk, 2) < 0) neg_z |= 1u << kk;
   }
   const int64_t cols = (int64_t)g.My * g.Hx;
-  VC_CHECK(cols < (1 << 30) && (int64_t)g.Hx * g.Oy * g.Oz < ((int64_t)1 << 31) && B < 65536,
+  VC_CHECK((cols + TX - 1) / TX < 65536 && (int64_t)g.Hx * g.Oy * g.Oz < ((int64_t)1 << 31),
            VOXCAP_ERR_UNSUPPORTED, "grid too large for the z pass");
-  dim3 grid((unsigned)((cols + TX - 1) / TX), B);
+  dim3 grid(B, (unsigned)((cols + TX - 1) / TX));
 #define VC_ZMAC(R)                                                                              \
   case R:                                                                                       \
     VC_TRY(set_smem(k_zmac<T, ADJ, R>, sm));                                                    \
