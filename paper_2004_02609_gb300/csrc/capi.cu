@@ -103,6 +103,7 @@ static int setup_impl(const int32_t* labels, int nx, int ny, int nz, int n_struc
   h.opts.tucker = nullptr;        // the caller's factors are not retained
   if ((rc = build_spectra(h))) return fail(rc);
   if ((rc = build_precond(h))) return fail(rc);
+  if ((rc = tune_products(h))) return fail(rc);
   *out = v;
   return VOXCAP_OK;
 }
@@ -248,6 +249,23 @@ int voxcap_canonical_tensors(int D, double* ppar, double* epar, double* port, do
 }
 
 int64_t voxcap_launch_count(void) { return vc::launch_count(); }
+
+int voxcap_set_zpass(voxcap_t* hv, int order, int tile_log2, int* order_out, int* tile_out) {
+  VC_CHECK(hv != nullptr, VOXCAP_ERR_ARG, "NULL handle");
+  Handle& h = hv->h;
+  VC_CHECK(order >= -1 && order <= 1 && (order < 0 || (tile_log2 >= 0 && tile_log2 <= 4)), VOXCAP_ERR_ARG,
+           "order must be -1, 0 or 1 and tile_log2 in 0..4");
+  set_alloc_stream(h.stream);
+  if (order < 0) {
+    VC_TRY(retune_products(h));
+  } else {
+    h.zvar = order < h.nzvar ? order : 0;
+    h.ztx = tile_log2;
+  }
+  if (order_out) *order_out = h.zvar;
+  if (tile_out) *tile_out = h.ztx;
+  return VOXCAP_OK;
+}
 
 int voxcap_fft_length(const voxcap_t* hv, int* mx, int* my, int* mz) {
   VC_CHECK(hv != nullptr, VOXCAP_ERR_ARG, "NULL handle");

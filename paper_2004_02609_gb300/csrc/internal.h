@@ -176,6 +176,13 @@ struct Handle {
   // with, so the two meet in registers
   Plan1D<double2> pdr[3];
   Plan1D<float2> pfr[3];
+  // z pass: forward/reversed plans of up to two radix orders (0: largest
+  // radix <= 9 last, 1: smallest radix last) and the tuned choice
+  int nzvar = 1;
+  Plan1D<double2> pzd[2], pzdr[2];
+  Plan1D<float2> pzf[2], pzfr[2];
+  int zvar = 0;                   // radix order of the z pass
+  int ztx = -1;                   // log2 of its tile width, -1: heuristic
   const double2* phd[3] = {nullptr, nullptr, nullptr};   // exp(+i pi k / M) per axis, k in [0, M)
   const float2* phf[3] = {nullptr, nullptr, nullptr};
   // Toeplitz tensors (FP64) and spectra
@@ -216,8 +223,14 @@ template <typename K> inline int set_smem(K kernel, size_t bytes) {
 }
 
 // The z pass of a product (z transforms, spectral multiply-accumulate,
-// inverse z transforms) over B batch items of the y/z-pass buffer, in place.
-template <typename T, bool ADJ> int zmac_launch(const Handle& h, C_t<T>* data, int B, cudaStream_t st);
+// inverse z transforms) over B batch items of the y/z-pass buffer, in place;
+// radix order `var` and tile width 2^tx_sh (tx_sh < 0: the handle's choice).
+template <typename T, bool ADJ>
+int zmac_launch(const Handle& h, C_t<T>* data, int B, cudaStream_t st, int var = -1, int tx_sh = -1);
+// Time the z-pass variants on this handle's own FP32 products and keep the
+// fastest (cached per grid shape and batch).
+int tune_products(Handle& h);
+int retune_products(Handle& h);   // the same, ignoring (and replacing) the cached choice
 
 // ---- module entry points (host side) ----
 int build_fft_plans(Handle& h);

@@ -152,30 +152,50 @@ int build_fft_plans(Handle& h) {
   int n[3] = {g.nx, g.ny, g.nz};
   int M[3];
   TableStage ts;
-  size_t off[3][6];
+  size_t off[3][6], zoff[2][4];
   for (int a = 0; a < 3; ++a) {
     M[a] = pick_length(n[a], h.opts.pad_mode);
     int rad[kMaxStages], nst = 0;
     VC_CHECK(factor_length(M[a], rad, &nst), VOXCAP_ERR_UNSUPPORTED,
              "FFT length " + std::to_string(M[a]) + " is not 2/3/5/7-smooth (use pad_mode 0)");
+    int zord[2][kMaxStages], zn[2] = {nst, nst};
     if (a == 2) {
-      // the z pass keeps its last forward radix in registers: the largest
-      // radix <= 9 goes last, and a last 16 (too many registers per line
-      // and grid) is split into 4 x 4
-      int best = -1;
-      for (int s = 0; s < nst; ++s)
-        if (rad[s] <= 9 && (best < 0 || rad[s] > rad[best])) best = s;
-      if (best < 0) best = 0;
-      std::swap(rad[best], rad[nst - 1]);
-      if (rad[nst - 1] == 16) {
-        rad[nst - 1] = 4;
-        rad[nst++] = 4;
+      // the z pass keeps its last forward radix in registers: order 0 puts the
+      // largest radix <= 9 last, order 1 the smallest (more threads per tile);
+      // a last 16 (too many registers per line and grid) is split into 4 x 4
+      for (int v = 0; v < 2; ++v) {
+        for (int s = 0; s < nst; ++s) zord[v][s] = rad[s];
+        int best = -1;
+        for (int s = 0; s < nst; ++s) {
+          const int R = zord[v][s];
+          if (v == 0 ? (R <= 9 && (best < 0 || R > zord[v][best])) : (best < 0 || R < zord[v][best])) best = s;
+        }
+        if (best < 0) best = 0;
+        std::swap(zord[v][best], zord[v][nst - 1]);
+        if (zord[v][nst - 1] == 16) {
+          zord[v][nst - 1] = 4;
+          zord[v][zn[v]++] = 4;
+        }
       }
+      for (int s = 0; s < zn[0]; ++s) rad[s] = zord[0][s];
+      nst = zn[0];
     }
     make_plan(M[a], rad, nst, ts, h.pd[a], h.pf[a], &off[a][0], &off[a][1], &off[a][2], &off[a][3]);
     int rev[kMaxStages];
     for (int s = 0; s < nst; ++s) rev[s] = rad[nst - 1 - s];
     make_plan(M[a], rev, nst, ts, h.pdr[a], h.pfr[a], &off[a][4], &off[a][5], nullptr, nullptr);
+    if (a == 2) {
+      h.nzvar = 1;
+      bool same = zn[1] == zn[0];
+      for (int s = 0; same && s < zn[0]; ++s) same = zord[1][s] == zord[0][s];
+      if (!same) h.nzvar = 2;
+      for (int v = 0; v < h.nzvar; ++v) {
+        int r2[kMaxStages];
+        for (int s = 0; s < zn[v]; ++s) r2[s] = zord[v][zn[v] - 1 - s];
+        make_plan(M[a], zord[v], zn[v], ts, h.pzd[v], h.pzf[v], &zoff[v][0], &zoff[v][1], nullptr, nullptr);
+        make_plan(M[a], r2, zn[v], ts, h.pzdr[v], h.pzfr[v], &zoff[v][2], &zoff[v][3], nullptr, nullptr);
+      }
+    }
   }
   VC_TRY(h.plan_tab.alloc(ts.bytes.size()));
   // from pageable memory: returns once the bytes are staged, so `ts` may go
@@ -189,6 +209,14 @@ int build_fft_plans(Handle& h) {
     h.pdr[a].stw = reinterpret_cast<const double2*>(base + off[a][4]);
     h.pfr[a].stw = reinterpret_cast<const float2*>(base + off[a][5]);
   }
+  for (int v = 0; v < h.nzvar; ++v) {
+    h.pzd[v].stw = reinterpret_cast<const double2*>(base + zoff[v][0]);
+    h.pzf[v].stw = reinterpret_cast<const float2*>(base + zoff[v][1]);
+    h.pzdr[v].stw = reinterpret_cast<const double2*>(base + zoff[v][2]);
+    h.pzfr[v].stw = reinterpret_cast<const float2*>(base + zoff[v][3]);
+  }
+  h.zvar = 0;
+  h.ztx = -1;
   g.Mx = M[0]; g.My = M[1]; g.Mz = M[2];
   g.Hx = g.Mx / 2 + 1;
   g.Oy = g.My / 2 + 1;

@@ -1,0 +1,81 @@
+// Set-up-time autotuning of the product's z pass: the radix order of its z
+// transform (largest radix <= 9 last, or smallest last) and its tile width
+// (8 or 16 columns) are timed on the handle's own FP32 products, all
+// conductor columns at once, and the fastest is kept.  The choice is cached
+// per device, grid and batch, so later set-ups of the same shape reuse it.
+#include <algorithm>
+#include <array>
+#include <map>
+#include <mutex>
+
+#include "internal.h"
+
+namespace vc {
+
+namespace {
+std::mutex g_tune_mu;
+std::map<std::array<int, 8>, std::array<int, 2>> g_tune;
+}  // namespace
+
+static int tune(Handle& h, bool use_cache) {
+  const int64_t N = h.pan.N;
+  if (N == 0) return VOXCAP_OK;
+  const int nrhs = std::max(1, h.pan.m_max);
+  const Geom& g = h.g;
+  const std::array<int, 8> key = {h.device, g.Mx, g.My, g.Mz, g.nx, g.ny, g.nz, h.pan.S * nrhs};
+  if (use_cache) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      h.zvar = it->second[0];
+      h.ztx = it->second[1];
+      return VOXCAP_OK;
+    }
+  }
+  DBuf<float> x, y;
+  VC_TRY(x.alloc((size_t)N * nrhs));
+  VC_TRY(y.alloc((size_t)N * nrhs));
+  VC_CUDA(cudaMemsetAsync(x.p, 0, sizeof(float) * (size_t)N * nrhs, h.stream));
+  VC_TRY(mvm_prepare(h, nrhs, sizeof(float2)));
+  cudaEvent_t e0, e1;
+  VC_CUDA(cudaEventCreate(&e0));
+  VC_CUDA(cudaEventCreate(&e1));
+  struct EvGuard {
+    cudaEvent_t a, b;
+    ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); }
+  } guard{e0, e1};
+  float best_ms = 1e30f;
+  int best_v = 0, best_tx = -1;
+  for (int v = 0; v < h.nzvar; ++v)
+    for (int tx : {4, 3}) {
+      h.zvar = v;
+      h.ztx = tx;
+      // a variant this grid cannot launch (a host-side check) is skipped
+      if (mvm<float>(h, x.p, y.p, nrhs, false, nullptr) != VOXCAP_OK) {
+        (void)cudaGetLastError();
+        continue;
+      }
+      VC_CUDA(cudaEventRecord(e0, h.stream));
+      for (int r = 0; r < 3; ++r) VC_TRY(mvm<float>(h, x.p, y.p, nrhs, false, nullptr));
+      VC_CUDA(cudaEventRecord(e1, h.stream));
+      VC_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.0f;
+      VC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best_ms) {
+        best_ms = ms;
+        best_v = v;
+        best_tx = tx;
+      }
+    }
+  VC_CHECK(best_ms < 1e30f, VOXCAP_ERR_UNSUPPORTED, "no z-pass variant fits this grid");
+  h.zvar = best_v;
+  h.ztx = best_tx;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = {best_v, best_tx};
+  return VOXCAP_OK;
+}
+
+int tune_products(Handle& h) { return tune(h, true); }
+int retune_products(Handle& h) { return tune(h, false); }
+
+}  // namespace vc

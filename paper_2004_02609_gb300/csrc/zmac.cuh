@@ -65,7 +65,7 @@ __device__ __forceinline__ T spec_at(const T* __restrict__ spec, int64_t Otot, i
 template <typename T, bool ADJ, int RL>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_zmac(Geom g, C_t<T>* __restrict__ data, const T* __restrict__ spec,
                                               Plan1D<C_t<T>> pf, Plan1D<C_t<T>> pv,
-                                              const C_t<T>* __restrict__ phz, int tx_sh,
+                                              const C_t<T>* __restrict__ phz, int tx_sh, int nbatch,
                                               uint32_t neg_y, uint32_t neg_z) {
   using C = C_t<T>;
   extern __shared__ unsigned char smem_raw[];
@@ -80,9 +80,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_zmac(Geom g, C_
   C* twv = twf + pf.twn;
   load_twiddles(twf, pf);
   load_twiddles(twv, pv);
-  const int b = blockIdx.x;                             // batch items of one tile run together
+  const int b = blockIdx.x % nbatch;                    // batch items of one tile run together
   const int64_t zstride = (int64_t)g.My * H;            // one z plane: [My][H], contiguous
-  const int q0 = blockIdx.y * TX;                       // first (ky, kx) column: q = ky * H + kx
+  const int q0 = (blockIdx.x / nbatch) * TX;            // first (ky, kx) column: q = ky * H + kx
   const int64_t gstride = (int64_t)g.Lz * zstride;      // one grid of one batch item
   C* base = data + (int64_t)b * 6 * gstride + q0;
   const int ncol = (int)min((int64_t)TX, zstride - q0); // valid columns of this tile
@@ -250,19 +250,35 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_zmac(Geom g, C_
            [&](int line, int pos) { return src[pos * LDO + line]; }, gstore);
 }
 
+template <typename T> inline const Plan1D<C_t<T>>& zplan(const Handle& h, int v, bool rev);
+template <> inline const Plan1D<float2>& zplan<float>(const Handle& h, int v, bool rev) {
+  return rev ? h.pzfr[v] : h.pzf[v];
+}
+template <> inline const Plan1D<double2>& zplan<double>(const Handle& h, int v, bool rev) {
+  return rev ? h.pzdr[v] : h.pzd[v];
+}
+
 template <typename T, bool ADJ>
-int zmac_launch(const Handle& h, C_t<T>* data, int B, cudaStream_t st) {
+int zmac_launch(const Handle& h, C_t<T>* data, int B, cudaStream_t st, int var, int tx_req) {
   using C = C_t<T>;
   const Geom& g = h.g;
-  const Plan1D<C>& pz = plan_of<T>(h, 2);
-  const Plan1D<C>& pzr = plan_rev_of<T>(h, 2);
+  if (var < 0) var = sizeof(T) == 4 ? h.zvar : 0;
+  if (var >= h.nzvar) var = 0;
+  if (tx_req < 0 && sizeof(T) == 4) tx_req = h.ztx;
+  const Plan1D<C>& pz = zplan<T>(h, var, false);
+  const Plan1D<C>& pzr = zplan<T>(h, var, true);
   const int RL = pz.radix[pz.nst - 1];
   const int nb = g.Mz / RL;
   const int nbuf = pz.nst >= 3 ? 2 : 1;
+  auto fits = [&](int sh) {
+    return (nb << sh) <= 256 && (size_t)nbuf * g.Mz * 6 * (1 << sh) * sizeof(C) <= 110 * 1024;
+  };
   int tx_sh = 4;
-  while (tx_sh > 0 && ((nb << tx_sh) > 256 ||
-                       (size_t)nbuf * g.Mz * 6 * (1 << tx_sh) * sizeof(C) > 110 * 1024))
-    --tx_sh;
+  if (tx_req >= 0 && tx_req <= 4 && fits(tx_req)) {
+    tx_sh = tx_req;
+  } else {
+    while (tx_sh > 0 && !fits(tx_sh)) --tx_sh;
+  }
   VC_CHECK((nb << tx_sh) <= 256, VOXCAP_ERR_UNSUPPORTED, "z transform too long for the fused z pass");
   const int TX = 1 << tx_sh;
   const int TB = std::max(64, ((nb << tx_sh) + 31) / 32 * 32);
@@ -273,14 +289,16 @@ int zmac_launch(const Handle& h, C_t<T>* data, int B, cudaStream_t st) {
     if (fold_sign(kk, 2) < 0) neg_z |= 1u << kk;
   }
   const int64_t cols = (int64_t)g.My * g.Hx;
-  VC_CHECK((cols + TX - 1) / TX < 65536 && (int64_t)g.Hx * g.Oy * g.Oz < ((int64_t)1 << 31),
+  const int64_t tiles = (cols + TX - 1) / TX;
+  VC_CHECK(tiles * B < ((int64_t)1 << 31) && (int64_t)g.Hx * g.Oy * g.Oz < ((int64_t)1 << 31),
            VOXCAP_ERR_UNSUPPORTED, "grid too large for the z pass");
-  dim3 grid(B, (unsigned)((cols + TX - 1) / TX));
+  // blockIdx.x = tile * B + item: the items of a tile are adjacent and share its spectra in L2
+  dim3 grid((unsigned)(tiles * B));
 #define VC_ZMAC(R)                                                                              \
   case R:                                                                                       \
     VC_TRY(set_smem(k_zmac<T, ADJ, R>, sm));                                                    \
     k_zmac<T, ADJ, R><<<grid, TB, sm, st>>>(g, data, spec_of<T>(h), pz, pzr, phase_of<T>(h, 2),  \
-                                            tx_sh, neg_y, neg_z);                               \
+                                            tx_sh, B, neg_y, neg_z);                               \
     break;
   switch (RL) {
     VC_ZMAC(2) VC_ZMAC(3) VC_ZMAC(4) VC_ZMAC(5) VC_ZMAC(7) VC_ZMAC(8) VC_ZMAC(9)

@@ -2,5 +2,5 @@
 #include "zmac.cuh"
 
 namespace vc {
-template int zmac_launch<float, false>(const Handle&, C_t<float>*, int, cudaStream_t);
+template int zmac_launch<float, false>(const Handle&, C_t<float>*, int, cudaStream_t, int, int);
 }  // namespace vc
