@@ -40,10 +40,21 @@ bool factor_length(int L, int* radix, int* nst) {
   int n = 0;
   int r = L;
   if (L < 1) return false;
-  while (r % 16 == 0 && n < kMaxStages) { radix[n++] = 16; r /= 16; }
-  while (r % 8 == 0 && n < kMaxStages) { radix[n++] = 8; r /= 8; }
-  while (r % 4 == 0 && n < kMaxStages) { radix[n++] = 4; r /= 4; }
-  while (r % 2 == 0 && n < kMaxStages) { radix[n++] = 2; r /= 2; }
+  // the power-of-two part 2^k in radices 16/8/4 without a radix-2 stage
+  // unless k = 1: k = 4a + 1 becomes 16^(a-1) 8 4
+  int k = 0;
+  while (r % 2 == 0) { ++k; r /= 2; }
+  if (k == 1) {
+    radix[n++] = 2;
+  } else if (k >= 2) {
+    int a = k / 4;
+    const int rem = k % 4;
+    if (rem == 1) --a;
+    for (int i = 0; i < a && n < kMaxStages; ++i) radix[n++] = 16;
+    if (rem == 1 && n + 1 < kMaxStages) { radix[n++] = 8; radix[n++] = 4; }
+    if (rem == 2 && n < kMaxStages) radix[n++] = 4;
+    if (rem == 3 && n < kMaxStages) radix[n++] = 8;
+  }
   while (r % 9 == 0 && n < kMaxStages) { radix[n++] = 9; r /= 9; }
   for (int p : {3, 5, 7})
     while (r % p == 0 && n < kMaxStages) { radix[n++] = p; r /= p; }
