@@ -136,7 +136,7 @@ def mvm_model_bytes(vc, nrhs):
 # kernels, from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum`
 # (profiles/product_traffic.md); None where no capture matches the current
 # kernels.
-TRAFFIC = {"plates": None, "bus": None}
+TRAFFIC = {"plates": 11909376, "bus": 4548623360}
 
 
 def product_roofline(vc, dev, reps, workload_name):
