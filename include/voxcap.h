@@ -337,20 +337,25 @@ int voxcap_toeplitz(const voxcap_t* h, int t, double* out_host, int* dims);
 int64_t voxcap_launch_count(void);
 
 /*
- * voxcap_set_zpass -- choose the z-pass variant of the handle's FP32 products
- * (an implementation choice with no counterpart in the paper; the z pass is
- * the z transform, spectral multiply-accumulate of Eqs. 11-12 and inverse z
- * transform of one product).  order: 0 = the z transform's largest radix
- * <= 9 last, 1 = its smallest radix last (ignored when both orders
- * coincide); tile_log2: log2 of the columns per CTA, 0..4 (a value that does
- * not fit falls back to the widest that does).  order = -1 re-runs the
- * set-up autotuner, which times the variants on this handle's own products
- * and keeps the fastest (its choice is cached per device, grid and batch).
- * order_out / tile_out (may be NULL) receive the choice in force.  Returns
- * VOXCAP_ERR_ARG for a NULL handle or an out-of-range argument.  Not safe
- * while another call on the same handle runs.
+ * voxcap_set_product_tiles -- choose the launch variant of the handle's FP32
+ * products (an implementation choice with no counterpart in the paper; the
+ * z pass is the z transform, spectral multiply-accumulate of Eqs. 11-12 and
+ * inverse z transform of one product, the y passes the transforms along y).
+ * z_order: 0 = the z transform's largest radix <= 9 last, 1 = its smallest
+ * radix last (ignored when both orders coincide); z_tile_log2: log2 of the
+ * z pass's columns per CTA, 0..4 (a width that does not fit falls back to
+ * the widest that does); y_fwd_log2 / y_inv_log2: log2 of the forward /
+ * inverse y passes' columns per CTA, 0..4, or -1 for the default width.
+ * z_order = -1 re-runs the set-up autotuner, which times the variants on
+ * this handle's own products and keeps the fastest (its choice is cached per
+ * device, grid and batch); the other arguments are then ignored.
+ * choice_out (may be NULL) receives {z_order, z_tile_log2, y_fwd_log2,
+ * y_inv_log2} in force.  Returns VOXCAP_ERR_ARG for a NULL handle or an
+ * out-of-range argument.  Not safe while another call on the same handle
+ * runs.
  */
-int voxcap_set_zpass(voxcap_t* h, int order, int tile_log2, int* order_out, int* tile_out);
+int voxcap_set_product_tiles(voxcap_t* h, int z_order, int z_tile_log2, int y_fwd_log2, int y_inv_log2,
+                             int* choice_out);
 
 #ifdef __cplusplus
 }

@@ -250,20 +250,30 @@ int voxcap_canonical_tensors(int D, double* ppar, double* epar, double* port, do
 
 int64_t voxcap_launch_count(void) { return vc::launch_count(); }
 
-int voxcap_set_zpass(voxcap_t* hv, int order, int tile_log2, int* order_out, int* tile_out) {
+int voxcap_set_product_tiles(voxcap_t* hv, int z_order, int z_tile_log2, int y_fwd_log2, int y_inv_log2,
+                             int* choice_out) {
   VC_CHECK(hv != nullptr, VOXCAP_ERR_ARG, "NULL handle");
   Handle& h = hv->h;
-  VC_CHECK(order >= -1 && order <= 1 && (order < 0 || (tile_log2 >= 0 && tile_log2 <= 4)), VOXCAP_ERR_ARG,
-           "order must be -1, 0 or 1 and tile_log2 in 0..4");
+  VC_CHECK(z_order >= -1 && z_order <= 1, VOXCAP_ERR_ARG, "z_order must be -1, 0 or 1");
+  if (z_order >= 0)
+    VC_CHECK(z_tile_log2 >= 0 && z_tile_log2 <= 4 && y_fwd_log2 >= -1 && y_fwd_log2 <= 4 &&
+                 y_inv_log2 >= -1 && y_inv_log2 <= 4,
+             VOXCAP_ERR_ARG, "tile widths out of range");
   set_alloc_stream(h.stream);
-  if (order < 0) {
+  if (z_order < 0) {
     VC_TRY(retune_products(h));
   } else {
-    h.zvar = order < h.nzvar ? order : 0;
-    h.ztx = tile_log2;
+    h.zvar = z_order < h.nzvar ? z_order : 0;
+    h.ztx = z_tile_log2;
+    h.ytx[0] = y_fwd_log2;
+    h.ytx[1] = y_inv_log2;
   }
-  if (order_out) *order_out = h.zvar;
-  if (tile_out) *tile_out = h.ztx;
+  if (choice_out) {
+    choice_out[0] = h.zvar;
+    choice_out[1] = h.ztx;
+    choice_out[2] = h.ytx[0];
+    choice_out[3] = h.ytx[1];
+  }
   return VOXCAP_OK;
 }
 

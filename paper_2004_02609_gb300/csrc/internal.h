@@ -183,6 +183,7 @@ struct Handle {
   Plan1D<float2> pzf[2], pzfr[2];
   int zvar = 0;                   // radix order of the z pass
   int ztx = -1;                   // log2 of its tile width, -1: heuristic
+  int ytx[2] = {-1, -1};          // log2 of the forward / inverse y passes' tile widths (FP32)
   const double2* phd[3] = {nullptr, nullptr, nullptr};   // exp(+i pi k / M) per axis, k in [0, M)
   const float2* phf[3] = {nullptr, nullptr, nullptr};
   // Toeplitz tensors (FP64) and spectra

@@ -311,14 +311,20 @@ int mvm(Handle& h, const T* x, T* y, int nrhs, bool adjoint, T* field_out, void*
     VC_CUDA(cudaGetLastError());
   }
   // yfwd: bufX [B][GI] -> bufY [B][6] (first GI grids)
-  const int TXy = smem_lines<T>(g.My, 1, 16);
+  // y tiles: the tuned widths for FP32 (4..16 columns), else the widest that fits
+  const int TXdef = smem_lines<T>(g.My, 1, 16);
+  const int TXf = (sizeof(T) == 4 && h.ytx[0] >= 0) ? (1 << h.ytx[0]) : TXdef;
+  const int TXi = (sizeof(T) == 4 && h.ytx[1] >= 0) ? (1 << h.ytx[1]) : TXdef;
+  const int ybufs = plan_of<T>(h, 1).nst >= 3 ? 2 : 1;
   {
-    size_t sm = ((plan_of<T>(h, 1).nst >= 3 ? 2 : 1) * (size_t)g.My * TXy + plan_of<T>(h, 1).twn) * sizeof(C);
+    const int TXy = TXf;
+    const int TBy = TXy >= 16 ? 256 : 128;
+    size_t sm = (ybufs * (size_t)g.My * TXy + plan_of<T>(h, 1).twn) * sizeof(C);
     dim3 grid((g.Hx + TXy - 1) / TXy, g.Lz, B * GI);
 #define VC_YFWD(W)                                                                          \
   VC_TRY(set_smem(k_ypass<T, false, W>, sm));                                            \
-  k_ypass<T, false, W><<<grid, TB, sm, st>>>(g, GI, bufX, bufY, (int64_t)GI * gX, (int64_t)6 * gY, \
-                                             plan_of<T>(h, 1), phase_of<T>(h, 1));
+  k_ypass<T, false, W><<<grid, TBy, sm, st>>>(g, GI, bufX, bufY, (int64_t)GI * gX, (int64_t)6 * gY, \
+                                              plan_of<T>(h, 1), phase_of<T>(h, 1));
     VC_TILE_DISPATCH(TXy, VC_YFWD)
 #undef VC_YFWD
     ::vc::note_launch();
@@ -329,12 +335,14 @@ int mvm(Handle& h, const T* x, T* y, int nrhs, bool adjoint, T* field_out, void*
   else VC_TRY((zmac_launch<T, false>(h, bufY, B, st)));
   // yinv: bufY [B][6] (first GO grids) -> bufX [B][GO]
   {
-    size_t sm = ((plan_of<T>(h, 1).nst >= 3 ? 2 : 1) * (size_t)g.My * TXy + plan_of<T>(h, 1).twn) * sizeof(C);
+    const int TXy = TXi;
+    const int TBy = TXy >= 16 ? 256 : 128;
+    size_t sm = (ybufs * (size_t)g.My * TXy + plan_of<T>(h, 1).twn) * sizeof(C);
     dim3 grid((g.Hx + TXy - 1) / TXy, g.Lz, B * GO);
 #define VC_YINV(W)                                                                         \
   VC_TRY(set_smem(k_ypass<T, true, W>, sm));                                            \
-  k_ypass<T, true, W><<<grid, TB, sm, st>>>(g, GO, bufY, bufX, (int64_t)6 * gY, (int64_t)GO * gX, \
-                                            plan_of<T>(h, 1), phase_of<T>(h, 1));
+  k_ypass<T, true, W><<<grid, TBy, sm, st>>>(g, GO, bufY, bufX, (int64_t)6 * gY, (int64_t)GO * gX, \
+                                             plan_of<T>(h, 1), phase_of<T>(h, 1));
     VC_TILE_DISPATCH(TXy, VC_YINV)
 #undef VC_YINV
     ::vc::note_launch();

@@ -1,6 +1,7 @@
-// Set-up-time autotuning of the product's z pass: the radix order of its z
+// Set-up-time autotuning of the product: the radix order of the z pass's
 // transform (largest radix <= 9 last, or smallest last) and its tile width
-// (8 or 16 columns) are timed on the handle's own FP32 products, all
+// (8 or 16 columns), then the tile widths of the inverse and forward y passes
+// (4, 8 or the default), are timed on the handle's own FP32 products, all
 // conductor columns at once, and the fastest is kept.  The choice is cached
 // per device, grid and batch, so later set-ups of the same shape reuse it.
 #include <algorithm>
@@ -14,7 +15,7 @@ namespace vc {
 
 namespace {
 std::mutex g_tune_mu;
-std::map<std::array<int, 8>, std::array<int, 2>> g_tune;
+std::map<std::array<int, 8>, std::array<int, 4>> g_tune;
 }  // namespace
 
 static int tune(Handle& h, bool use_cache) {
@@ -29,6 +30,8 @@ static int tune(Handle& h, bool use_cache) {
     if (it != g_tune.end()) {
       h.zvar = it->second[0];
       h.ztx = it->second[1];
+      h.ytx[0] = it->second[2];
+      h.ytx[1] = it->second[3];
       return VOXCAP_OK;
     }
   }
@@ -44,24 +47,30 @@ static int tune(Handle& h, bool use_cache) {
     cudaEvent_t a, b;
     ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); }
   } guard{e0, e1};
+  // times 3 products of the current choice (after one untimed); < 0 if it cannot launch
+  auto time_products = [&](float* ms) -> int {
+    if (mvm<float>(h, x.p, y.p, nrhs, false, nullptr) != VOXCAP_OK) {
+      (void)cudaGetLastError();
+      *ms = -1.0f;
+      return VOXCAP_OK;
+    }
+    VC_CUDA(cudaEventRecord(e0, h.stream));
+    for (int r = 0; r < 3; ++r) VC_TRY(mvm<float>(h, x.p, y.p, nrhs, false, nullptr));
+    VC_CUDA(cudaEventRecord(e1, h.stream));
+    VC_CUDA(cudaEventSynchronize(e1));
+    VC_CUDA(cudaEventElapsedTime(ms, e0, e1));
+    return VOXCAP_OK;
+  };
+  h.ytx[0] = h.ytx[1] = -1;
   float best_ms = 1e30f;
   int best_v = 0, best_tx = -1;
   for (int v = 0; v < h.nzvar; ++v)
     for (int tx : {4, 3}) {
       h.zvar = v;
       h.ztx = tx;
-      // a variant this grid cannot launch (a host-side check) is skipped
-      if (mvm<float>(h, x.p, y.p, nrhs, false, nullptr) != VOXCAP_OK) {
-        (void)cudaGetLastError();
-        continue;
-      }
-      VC_CUDA(cudaEventRecord(e0, h.stream));
-      for (int r = 0; r < 3; ++r) VC_TRY(mvm<float>(h, x.p, y.p, nrhs, false, nullptr));
-      VC_CUDA(cudaEventRecord(e1, h.stream));
-      VC_CUDA(cudaEventSynchronize(e1));
-      float ms = 0.0f;
-      VC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-      if (ms < best_ms) {
+      float ms;
+      VC_TRY(time_products(&ms));
+      if (ms >= 0.0f && ms < best_ms) {
         best_ms = ms;
         best_v = v;
         best_tx = tx;
@@ -70,8 +79,22 @@ static int tune(Handle& h, bool use_cache) {
   VC_CHECK(best_ms < 1e30f, VOXCAP_ERR_UNSUPPORTED, "no z-pass variant fits this grid");
   h.zvar = best_v;
   h.ztx = best_tx;
+  // then the tile widths of the inverse and the forward y passes (-1: the default)
+  for (int which : {1, 0}) {
+    int best_y = -1;
+    for (int t : {3, 2}) {
+      h.ytx[which] = t;
+      float ms;
+      VC_TRY(time_products(&ms));
+      if (ms >= 0.0f && ms < best_ms) {
+        best_ms = ms;
+        best_y = t;
+      }
+    }
+    h.ytx[which] = best_y;
+  }
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tune[key] = {best_v, best_tx};
+  g_tune[key] = {h.zvar, h.ztx, h.ytx[0], h.ytx[1]};
   return VOXCAP_OK;
 }
 

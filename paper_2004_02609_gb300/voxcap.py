@@ -30,7 +30,7 @@ SYMBOLS = ["voxcap_default_opts", "voxcap_last_error", "voxcap_setup", "voxcap_d
            "voxcap_capacitance", "voxcap_capacitance_grad", "voxcap_update_eps",
            "voxcap_entries", "voxcap_fft_length", "voxcap_toeplitz", "voxcap_launch_count",
            "voxcap_matvec_noalloc", "voxcap_tucker_expand", "voxcap_canonical_tensors",
-           "voxcap_set_zpass"]
+           "voxcap_set_product_tiles"]
 
 
 class Tucker(ctypes.Structure):
@@ -94,7 +94,7 @@ def lib():
         L.voxcap_matvec_noalloc.argtypes = [vp, vp, vp, i32, i32, i32]
         L.voxcap_tucker_expand.argtypes = [vp, i32, i32, i32, vp, i32, vp, i32, vp, i32, vp]
         L.voxcap_canonical_tensors.argtypes = [i32, vp, vp, vp, vp]
-        L.voxcap_set_zpass.argtypes = [vp, i32, i32, P(i32), P(i32)]
+        L.voxcap_set_product_tiles.argtypes = [vp, i32, i32, i32, i32, P(i32)]
         L.voxcap_launch_count.argtypes = []
         L.voxcap_launch_count.restype = ctypes.c_int64
         _LIB = L
@@ -204,13 +204,13 @@ class VoxCap:
     def n_conductors(self):
         return self.structs[0]["n_conductors"]
 
-    def set_zpass(self, order=-1, tile_log2=-1):
-        """Force the z-pass variant of the FP32 products (order 0/1, tile
-        width 2**tile_log2), or re-run the autotuner (order=-1); returns the
-        choice in force."""
-        o, t = ctypes.c_int(), ctypes.c_int()
-        _check(lib().voxcap_set_zpass(self._h, order, tile_log2, ctypes.byref(o), ctypes.byref(t)))
-        return o.value, t.value
+    def set_product_tiles(self, z_order=-1, z_tile_log2=4, y_fwd_log2=-1, y_inv_log2=-1):
+        """Force the launch variant of the FP32 products (z radix order 0/1,
+        tile widths as log2; -1 = default y width), or re-run the autotuner
+        (z_order=-1); returns the choice in force as a 4-tuple."""
+        out = (ctypes.c_int * 4)()
+        _check(lib().voxcap_set_product_tiles(self._h, z_order, z_tile_log2, y_fwd_log2, y_inv_log2, out))
+        return tuple(out)
 
     def fft_lengths(self):
         a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()

@@ -236,17 +236,19 @@ def test_matvec_every_radix(shape):
         assert rel_l2(yT[r], A.T @ X[r]) < 1e-12
         assert rel_l2(y32[r], A @ X[r]) < 2e-6
     assert radices
-    # every z-pass variant the autotuner may pick: both radix orders, tile widths 4..16
+    # every variant the autotuner may pick: both z radix orders, z tiles 4..16,
+    # y tiles 4..16 (forward and inverse)
     x32 = x64.float()
     for order in (0, 1):
         for tile in (2, 3, 4):
-            vc.set_zpass(order, tile)
-            f = vc.matvec(x32).cpu().numpy()
-            t = vc.matvec(x32, adjoint=True).cpu().numpy()
-            for r in range(2):
-                assert rel_l2(f[r], A @ X[r]) < 2e-6, (order, tile)
-                assert rel_l2(t[r], A.T @ X[r]) < 2e-6, (order, tile)
-    assert vc.set_zpass()[0] in (0, 1)
+            for yt in (-1, 2, 3):
+                vc.set_product_tiles(order, tile, yt, yt)
+                f = vc.matvec(x32).cpu().numpy()
+                t = vc.matvec(x32, adjoint=True).cpu().numpy()
+                for r in range(2):
+                    assert rel_l2(f[r], A @ X[r]) < 2e-6, (order, tile, yt)
+                    assert rel_l2(t[r], A.T @ X[r]) < 2e-6, (order, tile, yt)
+    assert vc.set_product_tiles()[0] in (0, 1)
 
 
 def test_matvec_paper_padding_equals_smooth_padding():
