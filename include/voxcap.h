@@ -64,12 +64,16 @@ extern "C" {
 #define VOXCAP_FP32_REFINE 1     /* FP32 GMRES / FP32 FFT products inside FP64 iterative refinement */
 
 /* precision of the generated Toeplitz entries (voxcap_opts.entries) */
-#define VOXCAP_ENTRIES_AUTO 0    /* FP32 far field under VOXCAP_FP32_REFINE, FP64 under VOXCAP_FP64 */
+#define VOXCAP_ENTRIES_AUTO 0    /* FP32 far field under VOXCAP_FP32_REFINE when the permittivity
+                                    contrast (max/min eps_r of the dielectric labels and the vacuum
+                                    outside) is at most 1e4, else FP64 */
 #define VOXCAP_ENTRIES_FP64 1    /* every entry in FP64 (near-field closed forms, far-field quadrature) */
 #define VOXCAP_ENTRIES_FAR32 2   /* near-field closed forms in FP64, far-field quadrature sums in FP32
                                     (entries to about 1e-7 relative, the FP32 products' accuracy);
                                     the kernel spectra are then transformed in FP32 as well and the
-                                    FP64 products use their widening */
+                                    FP64 products use their widening.  At high contrast the dielectric
+                                    rows' I' + E' nearly cancel and amplify entry errors by about the
+                                    contrast: FAR32 is meant for contrasts up to about 1e4 */
 
 /* dtypes of voxcap_matvec */
 #define VOXCAP_F32 0

@@ -1,4 +1,5 @@
 // extern "C" entry points declared in include/voxcap.h.
+#include <algorithm>
 #include <chrono>
 #include <cstring>
 #include <new>
@@ -66,8 +67,18 @@ static int setup_impl(const int32_t* labels, int nx, int ny, int nz, int n_struc
   if (h.opts.max_iters < 1) h.opts.max_iters = 2000;
   VC_CHECK(h.opts.entries >= VOXCAP_ENTRIES_AUTO && h.opts.entries <= VOXCAP_ENTRIES_FAR32, VOXCAP_ERR_ARG,
            "entries must be one of VOXCAP_ENTRIES_*");
+  // permittivity contrast (vacuum outside the grid included): on dielectric
+  // rows I' + E' nearly cancel at high contrast and amplify entry errors by
+  // about the contrast, so FP32 far-field sums are only automatic up to 1e4
+  double emin = 1.0, emax = 1.0;
+  for (int l = 0; l < n_labels; ++l)
+    if (conductor_id[l] < 0) {
+      emin = std::min(emin, eps_r[l]);
+      emax = std::max(emax, eps_r[l]);
+    }
   h.far32 = h.opts.entries == VOXCAP_ENTRIES_FAR32 ||
-            (h.opts.entries == VOXCAP_ENTRIES_AUTO && h.opts.precision == VOXCAP_FP32_REFINE);
+            (h.opts.entries == VOXCAP_ENTRIES_AUTO && h.opts.precision == VOXCAP_FP32_REFINE &&
+             emax <= 1e4 * emin);
   h.dv = voxel_size_m;
   h.nlab = n_labels;
   h.cid.assign(conductor_id, conductor_id + n_labels);
