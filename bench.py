@@ -167,6 +167,17 @@ def product_roofline(vc, dev, reps, workload_name):
                    "fft_lengths": list(vc.fft_lengths())}
 
 
+def max_over_ranks(x, world, device):
+    """The largest x over the ranks (the job's time is its slowest rank's)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
 def run_ours(args, rank, world):
     import torch
     import __graft_entry__ as ge
@@ -218,12 +229,7 @@ def run_ours(args, rank, world):
     barrier()
     launches = V.launch_count() - launches0
     t_step = sum(times) / len(times)
-    t_max = t_step
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([sum(times)], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = tt.item() / len(times)
+    t_max = max_over_ranks(sum(times), world, dev) / len(times)
     # ---- plain FP64 for comparison ----
     extraction("fp64", lab_dev)
     t64 = []
