@@ -199,7 +199,8 @@ struct Handle {
   DBuf<double> rhs;               // last capacitance RHS
   bool have_rho = false;
   DBuf<char> solver_ws;
-  HostMap act_map;                // GMRES: active flags per step parity, [2][nrhs]
+  HostMap act_map;                // GMRES: [2][nrhs] active flags per step parity, then the
+                                  // cycle-end read-back of iteration counts and flags [2][nrhs]
 };
 
 // ---- per-precision views of the handle's plans, phases and spectra

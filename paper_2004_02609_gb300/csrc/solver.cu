@@ -420,7 +420,7 @@ static int gmres(Handle& h, const T* r, T* d, int nrhs, double rtol, int max_it,
   unsigned* tickets = reinterpret_cast<unsigned*>(ip + 1);    // [nrhs] columns, [nrhs] the store
   VC_CUDA(cudaMemsetAsync(d, 0, sizeof(T) * nW, st));
   VC_CUDA(cudaMemsetAsync(tickets, 0, sizeof(unsigned) * (nrhs + 1), st));
-  VC_TRY(h.act_map.ensure((size_t)2 * nrhs));
+  VC_TRY(h.act_map.ensure((size_t)4 * nrhs));
   const int TB = 256;
   const unsigned gN = (unsigned)((N * nrhs + TB - 1) / TB);
   const unsigned gC = (unsigned)((nrhs + 63) / 64);
@@ -484,7 +484,6 @@ static int gmres(Handle& h, const T* r, T* d, int nrhs, double rtol, int max_it,
 
   bool first = true;
   int total_it = 0;
-  std::vector<int> its(nrhs);
   for (int cycle = 0; cycle < 100000; ++cycle) {
     // V0 = R (r - A d), vcur = V0 / ||V0||, j = 0
     if (first) {
@@ -526,23 +525,24 @@ static int gmres(Handle& h, const T* r, T* d, int nrhs, double rtol, int max_it,
       if (!any || checked >= m) done = true;
     }
     total_it += checked;
-    VC_CUDA(cudaStreamSynchronize(st));
     k_backsolve<<<gC, 64, 0, st>>>(s, nrhs, m); ::vc::note_launch();
     k_update_x<T><<<gN, TB, 0, st>>>(d, V, N, nrhs, s.hcol, s.kused, m); ::vc::note_launch();
+    // a column that stopped only because the cycle ended is still unconverged:
+    // re-activate it from the residual estimate (converged ones stay inactive)
+    k_reactivate<<<gC, 64, 0, st>>>(s, nrhs, m, rtol, max_it); ::vc::note_launch();
     VC_CUDA(cudaGetLastError());
-    // columns still unconverged after a full cycle restart; converged ones stay inactive
-    VC_CUDA(cudaMemcpyAsync(its.data(), s.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
+    // iteration counts and active flags in one read-back (mapped pinned host memory)
+    int* its_h = h.act_map.h + 2 * nrhs;
+    int* act_h = h.act_map.h + 3 * nrhs;
+    VC_CUDA(cudaMemcpyAsync(its_h, s.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
+    VC_CUDA(cudaMemcpyAsync(act_h, s.active, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
     VC_CUDA(cudaStreamSynchronize(st));
     int maxit = 0;
-    for (int c = 0; c < nrhs; ++c) maxit = std::max(maxit, its[c]);
-    // a column that stopped only because the cycle ended is still unconverged:
-    // re-activate it from the residual estimate
-    k_reactivate<<<gC, 64, 0, st>>>(s, nrhs, m, rtol, max_it); ::vc::note_launch();
-    std::vector<int> act(nrhs);
-    VC_CUDA(cudaMemcpyAsync(act.data(), s.active, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
-    VC_CUDA(cudaStreamSynchronize(st));
     bool any = false;
-    for (int c = 0; c < nrhs; ++c) any = any || act[c];
+    for (int c = 0; c < nrhs; ++c) {
+      maxit = std::max(maxit, its_h[c]);
+      any = any || act_h[c];
+    }
     if (!any || maxit >= max_it) break;
   }
   cnt->iters += total_it;
@@ -606,7 +606,8 @@ int solve(Handle& h, const double* B, int nrhs, double tol, double* X, voxcap_st
       k_sub<double><<<gN, TB, 0, s>>>(B, AX.p, R64.p, (int64_t)n); ::vc::note_launch();
       VC_CUDA(cudaGetLastError());
     }
-    VC_TRY(col_norms(h, R64.p, nrhs, rn, dpart.p, dnorm.p));
+    if (sw == 0) rn = bn;                            // the first residual is B itself
+    else VC_TRY(col_norms(h, R64.p, nrhs, rn, dpart.p, dnorm.p));
     worst = 0.0;
     std::vector<double> f(nrhs), finv(nrhs);
     double need = 0.0;   // largest reduction still needed
