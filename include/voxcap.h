@@ -120,9 +120,9 @@ typedef struct voxcap_opts {
                           1: the paper's M = 2(N+1) (must be 2/3/5/7-smooth);
                           2: the smallest even 2/3/5/7-smooth length */
   int entries;         /* VOXCAP_ENTRIES_* (default AUTO): precision of the generated entries */
-  const voxcap_tucker* tucker; /* NULL: generate the Toeplitz tensors in FP64 (Eqs. 5-6);
-                          else restore them from these Tucker factors on the
-                          tensor cores (Sec. II.C), cropped to the grid */
+  const voxcap_tucker* tucker; /* NULL: generate the Toeplitz tensors (Eqs. 5-6, precision
+                          per `entries`); else restore them from these Tucker
+                          factors on the tensor cores (Sec. II.C), cropped to the grid */
 } voxcap_opts;
 
 typedef struct voxcap_stats {
@@ -143,9 +143,14 @@ const char* voxcap_last_error(void);
 /*
  * voxcap_setup -- build everything the iterative solution needs (Sec. II):
  * panels from the voxel labels (Sec. II.A-B), the block-Toeplitz tensors of
- * Eqs. 5-6 on the device in FP64 (Appendix A-B), their block-circulant
- * embedding and its FFT (Eqs. 11-12, Appendix B), and the preconditioner
- * (Eq. 14).
+ * Eqs. 5-6 on the device (Appendix A-B; near field in FP64, far field in FP32
+ * or FP64 as opts->entries selects) or restored from Tucker factors, their
+ * block-circulant embedding and its FFT (Eqs. 11-12, Appendix B), and the
+ * preconditioner (Eq. 14; blocks of up to 224 panels are inverted in FP32,
+ * larger ones in FP64).  The first set-up of a grid shape and batch in a
+ * process also times the launch variants of the FP32 product on its own
+ * products and keeps the fastest (see voxcap_set_product_tiles); later
+ * set-ups of that shape reuse the choice.
  *
  *  labels       [n_struct][nz][ny][nx] int32, x fastest; host or device
  *               (detected with cudaPointerGetAttributes).  Each entry is a

@@ -1,4 +1,5 @@
-// Block-Toeplitz tensors of Eqs. 5-6 (Appendix A-B), evaluated in FP64.
+// Block-Toeplitz tensors of Eqs. 5-6 (Appendix A-B): near field in FP64, far
+// field in FP64 or, for the FP32-refinement set-up, with FP32 inner sums.
 //
 // Every one of the 15 tensors is one of four functions of the centre
 // difference of the two unit panels, up to an axis permutation:

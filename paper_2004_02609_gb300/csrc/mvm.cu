@@ -20,6 +20,8 @@
 //         gather at the panels
 // The transposed product runs the same passes with the panel values split
 // by row kind (6 input grids), the conjugated kernels and 3 output grids.
+// The z pass lives in zmac.cuh (one translation unit per precision and
+// direction); its variant and the y passes' tile widths are tuned at set-up.
 #include "internal.h"
 
 namespace vc {

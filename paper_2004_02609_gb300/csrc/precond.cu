@@ -11,7 +11,9 @@
 // (orientations and face offsets from the box corner) is identical have
 // identical blocks, so only one inverse per distinct pattern is stored
 // (Sec. II.D point (ii)).  BD uses all panels of a box (dielectric rows with
-// E' + I'), DIAG uses 1/A_kk and NONE the identity.
+// E' + I'), DIAG uses 1/A_kk and NONE the identity.  Inverses of blocks up to
+// 224 panels are computed in FP32 by one CTA each (a preconditioner only
+// steers GMRES); larger blocks by a multi-CTA FP64 Gauss-Jordan.
 #include <algorithm>
 #include <vector>
 
