@@ -105,40 +105,6 @@ struct GState {      // per-column GMRES state, FP64, device
   int* iters;        // [nrhs] total iterations
 };
 
-// After the two Gram-Schmidt passes: H[:,j] = hcol + hcol2, h_{j+1,j} = sqrt(nrm2);
-// Givens update; convergence test; scale factor for the new basis vector.
-__global__ void k_givens(GState s, int nrhs, int m, int j, double rtol, int max_it, double* inv_norm) {
-  const int col = blockIdx.x * blockDim.x + threadIdx.x;
-  if (col >= nrhs) return;
-  if (!s.active[col]) { inv_norm[col] = 0.0; return; }
-  double* H = s.H + (int64_t)col * (m + 1) * m + (int64_t)j * (m + 1);
-  double* cs = s.cs + (int64_t)col * m;
-  double* sn = s.sn + (int64_t)col * m;
-  double* g = s.g + (int64_t)col * (m + 1);
-  for (int i = 0; i <= j; ++i) H[i] = s.hcol[(int64_t)col * (m + 1) + i] + s.hcol2[(int64_t)col * (m + 1) + i];
-  double hn = sqrt(fmax(s.nrm2[col], 0.0));
-  H[j + 1] = hn;
-  for (int i = 0; i < j; ++i) {
-    double t = cs[i] * H[i] + sn[i] * H[i + 1];
-    H[i + 1] = -sn[i] * H[i] + cs[i] * H[i + 1];
-    H[i] = t;
-  }
-  double den = hypot(H[j], H[j + 1]);
-  double c = den > 0.0 ? H[j] / den : 1.0;
-  double sv = den > 0.0 ? H[j + 1] / den : 0.0;
-  cs[j] = c;
-  sn[j] = sv;
-  H[j] = den;
-  H[j + 1] = 0.0;
-  g[j + 1] = -sv * g[j];
-  g[j] = c * g[j];
-  s.kused[col] = j + 1;
-  s.iters[col] += 1;
-  const bool conv = fabs(g[j + 1]) <= rtol * s.beta0[col];
-  if (conv || hn == 0.0 || s.iters[col] >= max_it) s.active[col] = 0;
-  inv_norm[col] = hn > 0.0 ? 1.0 / hn : 0.0;
-}
-
 template <typename T>
 __global__ void k_scale_cols(T* __restrict__ v, int64_t N, int nrhs, const double* __restrict__ f,
                              const int* __restrict__ mask) {
