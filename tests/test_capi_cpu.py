@@ -77,3 +77,44 @@ def test_struct_layouts_match_header(tmp_path, libpath):
     want = [ctypes.sizeof(V.Opts), ctypes.sizeof(V.Stats), ctypes.sizeof(V.Tucker),
             V.Opts.tucker.offset, V.Opts.pad_mode.offset, V.Opts.entries.offset, V.Tucker.factor.offset]
     assert got == want
+
+
+def test_argument_checks_before_any_device_work(libpath):
+    """Invalid arguments of every entry point that takes a handle, a size or a
+    table are rejected with VOXCAP_ERR_ARG (-1) and a message, before any CUDA
+    call (so this runs without a GPU)."""
+    import ctypes
+    import numpy as np
+    from paper_2004_02609_gb300 import voxcap as V
+    L = V.lib()
+    lab = np.zeros(8, np.int32)
+    cid = np.array([-1, 0], np.int32)
+    eps = np.array([1.0, 1.0])
+    h = ctypes.c_void_p()
+    P = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    cases = {
+        "non-positive grid": lambda: L.voxcap_setup(P(lab), 0, 2, 2, 1, P(cid), P(eps), 2, 1e-6, None, None,
+                                                    ctypes.byref(h)),
+        "non-positive voxel": lambda: L.voxcap_setup(P(lab), 2, 2, 2, 1, P(cid), P(eps), 2, 0.0, None, None,
+                                                     ctypes.byref(h)),
+        "bad conductor id": lambda: L.voxcap_setup(P(lab), 2, 2, 2, 1, P(np.array([-2, 0], np.int32)), P(eps),
+                                                   2, 1e-6, None, None, ctypes.byref(h)),
+        "bad permittivity": lambda: L.voxcap_setup(P(lab), 2, 2, 2, 1, P(cid), P(np.array([-1.0, 1.0])), 2,
+                                                   1e-6, None, None, ctypes.byref(h)),
+        "NULL out": lambda: L.voxcap_setup(P(lab), 2, 2, 2, 1, P(cid), P(eps), 2, 1e-6, None, None, None),
+        "matvec NULL handle": lambda: L.voxcap_matvec(None, None, None, 1, 0, 0),
+        "solve NULL handle": lambda: L.voxcap_solve(None, None, 1, 1e-6, None, None),
+        "capacitance NULL handle": lambda: L.voxcap_capacitance(None, 1e-6, None, None, None),
+        "gradient NULL handle": lambda: L.voxcap_capacitance_grad(None, None, 1e-6, None, None),
+        "update_eps NULL handle": lambda: L.voxcap_update_eps(None, None),
+        "panel map NULL handle": lambda: L.voxcap_panel_map(None, 0, None, None, None, None, None, None),
+        "toeplitz NULL handle": lambda: L.voxcap_toeplitz(None, 0, None, None),
+        "product tiles NULL handle": lambda: L.voxcap_set_product_tiles(None, 0, 4, -1, -1, None),
+    }
+    for name, call in cases.items():
+        rc = call()
+        assert rc == -1, (name, rc)
+        assert L.voxcap_last_error(), name
+    assert not h.value
+    o = V.default_opts(entries="fp64")
+    assert o.entries == V.ENTRIES["fp64"]
