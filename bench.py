@@ -28,6 +28,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -68,8 +69,8 @@ class ClockSampler:
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index):
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
-        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        fd, self.path = tempfile.mkstemp(prefix="voxcap_clocks_", suffix=".csv")
+        os.close(fd)
         self.proc = None
         self.gpu = gpu_index
 
@@ -95,6 +96,7 @@ class ClockSampler:
     def summary(self):
         try:
             rows = [l.strip().split(",") for l in open(self.path) if l.strip()]
+            os.remove(self.path)
         except Exception:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         sm, mx, reasons = [], [], set()

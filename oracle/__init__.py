@@ -26,7 +26,7 @@ Normalised units: voxel edge 1 and G' = 1/(4 pi r).  A physical system with
 voxel edge dv scales P by dv^3/eps0 and E, I by dv^2/eps0 (Appendix C); the
 charges then scale as rho = (eps0/dv) rho' and C = eps0 * dv * C'.
 
-Readings of the paper that this oracle takes (the same list is in the design doc):
+Readings of the paper that this oracle takes:
 * every panel normal is the +axis direction; side ``a`` is the voxel on the
   -axis side of the face and side ``b`` the +axis side; a dielectric panel has
   I' = (eps_a + eps_b) / (2 (eps_a - eps_b)) (Eq. 7 with the normal oriented
