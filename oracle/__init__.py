@@ -21,6 +21,11 @@ each function citing the passage it follows (arxiv 2004.02609):
                         comparison in Sec. III.A.
 * ``capacitance_grad`` -- dC/d(eps) by a dense adjoint solve.
 * ``tucker_hosvd`` / ``tucker_expand`` -- Eq. 13 (truncated HOSVD, einsum).
+* ``fft_gmres``      -- (module) the FFT-accelerated product of Eqs. 9-11 by
+                        directly evaluated circulant kernels and scipy FFTs,
+                        and GMRES(35) (Sec. III) on it: the CPU counterpart of
+                        the method for grids too large for the dense LU,
+                        checked against ``dense_matrix`` on small grids.
 
 Normalised units: voxel edge 1 and G' = 1/(4 pi r).  A physical system with
 voxel edge dv scales P by dv^3/eps0 and E, I by dv^2/eps0 (Appendix C); the
