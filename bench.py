@@ -50,6 +50,9 @@ def workload(name):
         return W.bus_crossing(), "4x4 bus crossing in 3 dielectric layers, 128x128x64 grid"
     if name == "pillars":
         return W.pillars_field()[0], "two pillars in a smooth random dielectric, 64^3 grid"
+    if name == "meanders":
+        return W.meanders(), ("two interleaved meanders (width 4, spacing 4, thickness 8, 32 legs) "
+                              "in eps_r=3.9, 512x512x64 grid")
     raise SystemExit(f"unknown workload {name}")
 
 

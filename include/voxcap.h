@@ -109,7 +109,8 @@ typedef struct voxcap_tucker {
 typedef struct voxcap_opts {
   int precision;       /* VOXCAP_FP64 or VOXCAP_FP32_REFINE (default) */
   int restart;         /* GMRES restart length (default 35, Sec. III) */
-  double inner_tol;    /* FP32 inner GMRES relative tolerance per refinement sweep (default 1e-4) */
+  double inner_tol;    /* FP32 inner GMRES: tightest relative tolerance of one refinement sweep
+                          (default 1e-4); a sweep stops earlier when that already meets tol */
   int max_iters;       /* cap on GMRES iterations per solve (default 2000) */
   int max_sweeps;      /* cap on refinement sweeps (default 20) */
   int nv[3];           /* small-box size of the preconditioner in voxels (default 10, Sec. II.D) */
@@ -222,7 +223,8 @@ int voxcap_matvec(voxcap_t* h, const void* x_dev, void* y_dev, int nrhs, int dty
  * cannot afford the implicit device synchronisation of cudaMalloc / cudaFree
  * cannot accept that.  This entry point calls no cudaMalloc, cudaFree or
  * allocating library routine: its scratch is one fixed 16 MiB array in the
- * library's device image, which every GPU that loads the library holds until
+ * library's device image.  A device holds it from the first call on that
+ * device (which loads the library's device module, array included) until
  * the process exits.
  *
  * Limits and sharing: a call whose scratch would exceed 16 MiB (it grows with
@@ -232,8 +234,9 @@ int voxcap_matvec(voxcap_t* h, const void* x_dev, void* y_dev, int nrhs, int dty
  * every element a call reads is written earlier in the same call, so nothing
  * has to start at zero.  Calls that overlap on the GPU (issued on different
  * streams or from different threads without ordering) race on the array.
- * The first call on a device looks up the array's device address on that
- * device (a set-up step); make that first call before any stream capture.
+ * Every call looks up the array's device address with the handle's device
+ * current; the first call on a device also loads the module there (a set-up
+ * step), so make that first call before any stream capture.
  */
 int voxcap_matvec_noalloc(voxcap_t* h, const void* x_dev, void* y_dev, int nrhs, int dtype,
                           int flags);

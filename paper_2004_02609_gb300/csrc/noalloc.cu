@@ -5,10 +5,9 @@
 // allocates (and grows) on first use, and its preconditioned form allocates
 // one more temporary per call.  This variant takes all of that scratch from
 // one fixed array in the library's device image instead, so the call itself
-// issues no cudaMalloc / cudaFree.  Every GPU that loads the library holds
-// the array until the process exits.
-#include <mutex>
-
+// issues no cudaMalloc / cudaFree.  The array belongs to the library's
+// device module: a device holds it from the first call there (which loads
+// the module) until the process exits.
 #include "internal.h"
 
 namespace vc {
@@ -18,26 +17,22 @@ constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-// Device address of g_noalloc_scratch per device.  In host code the array's
-// name is only a host-side stand-in, so the address is looked up once per
-// device, with that device current.
-static void* g_scratch_addr[128] = {nullptr};
-static std::mutex g_scratch_mu;
-
-static int noalloc_scratch(int dev, void** out) {
-  VC_CHECK(dev >= 0 && dev < 128, VOXCAP_ERR_ARG, "device ordinal out of range");
-  std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || p == nullptr) {
-      set_error(std::string("cudaGetSymbolAddress of the no-allocation scratch failed: ") +
-                cudaGetErrorString(e));
-      return VOXCAP_ERR_CUDA;
-    }
-    g_scratch_addr[dev] = p;
+// Device address of g_noalloc_scratch on the current device.  In host code
+// the array's name is only a host-side stand-in, so the address is looked up
+// with the handle's device current, on every call: the lookup is cheap once
+// the library's module is loaded on the device (the first lookup loads it,
+// together with the array), and a fresh lookup stays valid after the
+// device's context has been torn down and re-created.
+static int noalloc_scratch(void** out) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || p == nullptr) {
+    (void)cudaGetLastError();
+    set_error(std::string("cudaGetSymbolAddress of the no-allocation scratch failed: ") +
+              cudaGetErrorString(e));
+    return VOXCAP_ERR_CUDA;
   }
-  *out = g_scratch_addr[dev];
+  *out = p;
   return VOXCAP_OK;
 }
 
@@ -84,7 +79,7 @@ extern "C" int voxcap_matvec_noalloc(voxcap_t* hv, const void* x_dev, void* y_de
   VC_CUDA(cudaGetDevice(&cur));
   if (cur != h.device) VC_CUDA(cudaSetDevice(h.device));
   void* scratch = nullptr;
-  int rc = noalloc_scratch(h.device, &scratch);
+  int rc = noalloc_scratch(&scratch);
   if (rc == VOXCAP_OK) {
     if (dtype == VOXCAP_F32)
       rc = matvec_noalloc_impl<float>(h, (const float*)x_dev, (float*)y_dev, nrhs, flags, scratch);

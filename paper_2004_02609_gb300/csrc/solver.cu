@@ -589,11 +589,18 @@ int solve(Handle& h, const double* B, int nrhs, double tol, double* X, voxcap_st
     if (worst <= tol) { conv = true; break; }
     if (sw == max_sweeps || cnt.iters >= h.opts.max_iters) break;
     ++sweeps;
-    // inner tolerance: aim to finish in this sweep, within what the inner
-    // precision can deliver
-    double floor_t = refine ? 5e-6 : 1e-14;
-    double cap = refine ? std::max(h.opts.inner_tol, floor_t) : 1e-2;
-    double itol = std::min(cap, std::max(floor_t, 0.5 * need));
+    // inner tolerance.  Plain FP64: aim to finish in this sweep.  FP32 inside
+    // refinement: a sweep reduces its residual by inner_tol at most (FP32
+    // GMRES stagnates when pushed much further, and its Krylov space is
+    // rebuilt each sweep anyway) and by no more than finishing needs, so the
+    // last sweep does not over-solve
+    double itol;
+    if (refine) {
+      const double floor_t = 5e-6;
+      itol = std::max(floor_t, std::max(h.opts.inner_tol, 0.5 * need));
+    } else {
+      itol = std::min(1e-2, std::max(1e-14, 0.5 * need));
+    }
     int left = std::max(1, h.opts.max_iters - cnt.iters);
     VC_CUDA(cudaMemcpyAsync(fac.p, f.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
     if (refine) {

@@ -116,7 +116,12 @@ def test_pillars_gradient_by_central_differences(pillars):
     g, _ = vc.capacitance_grad(G, tol=1e-12)
     eps = wl.eps_r.copy()
     order = np.argsort(-np.abs(g))
-    picks = list(order[:6]) + list(order[200:202])
+    # the six largest gradients and two more drawn from the voxels whose
+    # gradient is at least 5% of the largest: each is far above the noise of
+    # the central difference (solves at 1e-12 give ~1e-8 |C| / step)
+    gmax = np.abs(g[order[0]])
+    rest = [v for v in order[6:] if np.abs(g[v]) >= 0.05 * gmax]
+    picks = list(order[:6]) + list(np.random.default_rng(7).choice(rest, 2, replace=False))
     h = 1e-4
     for v in picks:
         ep, em = eps.copy(), eps.copy()
@@ -127,7 +132,7 @@ def test_pillars_gradient_by_central_differences(pillars):
         vc.update_eps(em)
         Cm, _ = vc.capacitance(tol=1e-12)
         fd = (Cp[0, 1] - Cm[0, 1]) / (2 * h)
-        assert abs(fd - g[v]) <= 1e-3 * abs(fd) + 1e-4 * np.max(np.abs(g)), (v, fd, g[v])
+        assert abs(fd - g[v]) <= 1e-3 * abs(fd), (v, fd, g[v])
     vc.update_eps(eps)
     lay = torch.as_tensor(layer)
     bse = torch.as_tensor(base, dtype=torch.float64)

@@ -381,6 +381,58 @@ def test_preconditioner_blocks_invert_their_boxes():
     assert O.unique_box_patterns(ps, 5) >= 1
 
 
+@pytest.mark.parametrize("nx,ny,expect_boxes,expect_unique", [(20, 5, 4, 3), (20, 20, 16, 9)])
+def test_unique_box_patterns_hand_counted(nx, ny, expect_boxes, expect_unique):
+    """Sec. II.D (ii): a full conductor slab nx x ny x 1, boxes of 5 voxels.
+
+    Panels: x-faces at i = 0 and i = nx, y-faces at j = 0 and j = ny, z-faces
+    at k = 0 and k = 1 over the whole slab.  A face on the far boundary of its
+    own axis (i = nx, j = ny, k = 1) joins the last box along that axis.  Along
+    x the boxes fall into three classes: the first holds the i = 0 x-faces at
+    local x 0, the last holds the i = nx x-faces at local x 5, the middle ones
+    hold none; the same three classes along y (when ny > 5).  z-faces and the
+    z extent are identical in every box.  So a 4 x 1 row of boxes has the
+    patterns {first, middle, middle, last}: 3 unique; a 4 x 4 array has
+    3 x 3 = 9 unique patterns among its 16 boxes."""
+    lab = np.zeros((1, ny, nx), np.int32)
+    ps = O.panels(lab, np.array([0]), np.array([1.0]))
+    assert ps.n == 2 * ny + 2 * nx + 2 * nx * ny
+    box = O.panel_boxes(ps, 5)
+    assert len(np.unique(box)) == expect_boxes
+    assert O.unique_box_patterns(ps, 5) == expect_unique
+
+
+def _three_panel_set():
+    """Three z-normal panels on a 10 x 5 x 1 grid: panel 0 at z-face (1,1,0)
+    and panel 1 at (3,2,1) lie in box 0 (x in [0,5)), panel 2 at (7,0,0) in
+    box 1; panel 1 is a dielectric row with I' = 2.5."""
+    fx, fy = 10, 5                                   # z-face grid is 10 x 5 x 2
+    face = np.array([1 + fx * (1 + fy * 0), 3 + fx * (2 + fy * 1), 7 + fx * (0 + fy * 0)], np.int32)
+    n = 3
+    ps = O.PanelSet(10, 5, 1, np.full(n, 2, np.int8), face, np.array([0, 1, 0], np.int8),
+                    np.array([0, -1, 0], np.int16), np.array([0.0, 2.5, 0.0]), np.array([1.0, 0.0, 1.0]),
+                    np.zeros(n, np.int32), np.zeros(n, np.int32), 1, centers=np.zeros((n, 3)))
+    A = np.array([[2.0, 1.0, 0.5], [1.0, 4.0, 1.0], [0.5, 1.0, 8.0]])
+    return ps, A
+
+
+def test_preconditioner_variants_by_hand():
+    """Eq. 14 and the conventional preconditioners of Sec. III.A on a
+    three-panel case worked by hand (A = [[2,1,.5],[1,4,1],[.5,1,8]]):
+    diag = diag(1/2, 1/4, 1/8); bd = inv([[2,1],[1,4]]) = [[4,-1],[-1,2]]/7 on
+    box 0 and 1/8 on box 1; bdd = 1/2 and 1/8 on the conductor rows (each
+    alone in its box) and 1/I' = 0.4 on the dielectric row; none = I."""
+    ps, A = _three_panel_set()
+    assert list(O.panel_boxes(ps, 5)) == [0, 0, 1]
+    np.testing.assert_allclose(O.precond_matrix(ps, A, 5, "diag"), np.diag([0.5, 0.25, 0.125]),
+                               rtol=0, atol=1e-15)
+    bd = np.array([[4 / 7, -1 / 7, 0], [-1 / 7, 2 / 7, 0], [0, 0, 1 / 8]])
+    np.testing.assert_allclose(O.precond_matrix(ps, A, 5, "bd"), bd, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(O.precond_matrix(ps, A, 5, "bdd"), np.diag([0.5, 0.4, 0.125]),
+                               rtol=0, atol=1e-15)
+    np.testing.assert_array_equal(O.precond_matrix(ps, A, 5, "none"), np.eye(3))
+
+
 def test_oracle_gradient_matches_finite_differences():
     """The oracle's adjoint dC/d(eps) against central differences of its own
     capacitance (step 1e-4) on a tiny grid with distinct permittivities."""
