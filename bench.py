@@ -316,6 +316,8 @@ def run_products(args):
     ge.build()
     w, desc = workload(args.workload)
     vc = V.VoxCap(torch.tensor(w.labels, device="cuda"), w.conductor_id, w.eps_r, w.voxel_size)
+    if args.path >= 0:
+        vc.set_product_path(args.path)
     m = vc.n_conductors
     x = torch.randn(m, vc.N, device="cuda", dtype=torch.float32)
     for _ in range(args.warmup):
@@ -330,7 +332,7 @@ def run_products(args):
     t = e0.elapsed_time(e1) / 1e3 / args.steps
     hbm, src = read_peaks()
     b = mvm_model_bytes(vc, m) * m
-    return {"mode": "products", "workload": desc, "panels": vc.N, "columns": m,
+    return {"mode": "products", "workload": desc, "panels": vc.N, "columns": m, "path": vc.set_product_path(args.path) if args.path >= 0 else None,
             "fft_lengths": vc.fft_lengths(), "s_per_batched_product": t, "matvecs_per_s": m / t,
             "model_bytes": b, "achieved_GBps": b / t / 1e9, "frac_of_" + src + "_hbm": b / t / 1e9 / hbm}
 
@@ -420,6 +422,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--products", action="store_true",
                     help="time only the batched FP32 products of the workload (profiling aid)")
+    ap.add_argument("--path", type=int, default=-1,
+                    help="with --products: FP32 product kernels 0 generic, 1 compiled plans, -1 tuned")
     args = ap.parse_args()
     if args.products:
         print(json.dumps(run_products(args)), flush=True)

@@ -362,12 +362,30 @@ int64_t voxcap_launch_count(void);
  * this handle's own products and keeps the fastest (its choice is cached per
  * device, grid and batch); the other arguments are then ignored.
  * choice_out (may be NULL) receives {z_order, z_tile_log2, y_fwd_log2,
- * y_inv_log2} in force.  Returns VOXCAP_ERR_ARG for a NULL handle or an
- * out-of-range argument.  Not safe while another call on the same handle
- * runs.
+ * y_inv_log2} in force.  Forcing a variant (z_order >= 0) selects the
+ * generic passes (product path 0, see voxcap_set_product_path).  Returns
+ * VOXCAP_ERR_ARG for a NULL handle or an out-of-range argument.  Not safe
+ * while another call on the same handle runs.
  */
 int voxcap_set_product_tiles(voxcap_t* h, int z_order, int z_tile_log2, int y_fwd_log2, int y_inv_log2,
                              int* choice_out);
+
+/*
+ * voxcap_set_product_path -- which kernels run the handle's FP32 products
+ * (Eqs. 9-12; an implementation choice, same results to rounding):
+ *  path 0   the generic passes (any padded length; the FP64 products always
+ *           use them);
+ *  path 1   passes compiled for fixed radix plans wherever the padded length
+ *           of an axis has one (y: 36, 72, 144, 288, 576, 1152; z: 36, 72,
+ *           144; forward z pass only), the generic passes elsewhere;
+ *  path -1  re-run the set-up autotuner, which times both on this handle's
+ *           own products and keeps the faster (cached per device, grid and
+ *           batch).
+ *  path_out (may be NULL) receives the path in force.  Returns
+ * VOXCAP_ERR_ARG for a NULL handle or a path outside -1..1.  Not safe while
+ * another call on the same handle runs.
+ */
+int voxcap_set_product_path(voxcap_t* h, int path, int* path_out);
 
 #ifdef __cplusplus
 }

@@ -59,6 +59,24 @@ class FFTProduct:
                     circ[nz_ % Mz, ny_ % My, nx_ % Mx] = vals
                     self.K[(kind, a, b)] = sfft.rfftn(circ, workers=workers)
 
+    @classmethod
+    def timing_stand_in(cls, ps, workers: int | None = None):
+        """The same product with every kernel spectrum replaced by one shared
+        array of ones, for timing grids whose kernels are too many to
+        integrate here: the FFTs, the multiply-accumulate and the scatter /
+        gather do exactly the work of the real product, whose cost does not
+        depend on the spectra's values.  Its results are meaningless."""
+        self = cls.__new__(cls)
+        self.ps = ps
+        self.workers = workers
+        self.M = (2 * (ps.nx + 1), 2 * (ps.ny + 1), 2 * (ps.nz + 1))
+        self.F = [face_grid_dims(ps.nx, ps.ny, ps.nz, o) for o in range(3)]
+        self.ijk = face_coords(ps)
+        Mx, My, Mz = self.M
+        ones = np.ones((Mz, My, Mx // 2 + 1), np.complex128)
+        self.K = {(kind, a, b): ones for kind in (0, 1) for a in range(3) for b in range(3)}
+        return self
+
     def __call__(self, x: np.ndarray) -> np.ndarray:
         ps = self.ps
         Mx, My, Mz = self.M

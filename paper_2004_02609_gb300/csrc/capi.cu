@@ -274,6 +274,7 @@ int voxcap_set_product_tiles(voxcap_t* hv, int z_order, int z_tile_log2, int y_f
   if (z_order < 0) {
     VC_TRY(retune_products(h));
   } else {
+    h.path = 0;                       // a forced variant is one of the generic passes
     h.zvar = z_order < h.nzvar ? z_order : 0;
     h.ztx = z_tile_log2;
     h.ytx[0] = y_fwd_log2;
@@ -285,6 +286,21 @@ int voxcap_set_product_tiles(voxcap_t* hv, int z_order, int z_tile_log2, int y_f
     choice_out[2] = h.ytx[0];
     choice_out[3] = h.ytx[1];
   }
+  return VOXCAP_OK;
+}
+
+int voxcap_set_product_path(voxcap_t* hv, int path, int* path_out) {
+  VC_CHECK(hv != nullptr, VOXCAP_ERR_ARG, "NULL handle");
+  VC_CHECK(path >= -1 && path <= 1, VOXCAP_ERR_ARG, "path must be -1, 0 or 1");
+  Handle& h = hv->h;
+  set_alloc_stream(h.stream);
+  if (path < 0) {
+    VC_TRY(retune_products(h));
+  } else {
+    h.path = path;
+    h.yvar = 0;
+  }
+  if (path_out) *path_out = h.path;
   return VOXCAP_OK;
 }
 

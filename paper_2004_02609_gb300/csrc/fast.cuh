@@ -1,0 +1,133 @@
+// Compile-time Stockham stages for the FP32 products on the common padded
+// lengths (2^a and 2^a * 9 with two or three radix stages): the length, the
+// radices, the tile width and the thread count are template parameters, so
+// every index of a stage is constant-folded, and a tile needs one shared-
+// memory buffer (a middle stage runs in place: each thread holds all of its
+// butterflies in registers across a barrier).  Used by the passes in
+// fast_{x,y,z}.cu; the generic passes in mvm.cu / zmac.cuh cover every other
+// length and the FP64 products.
+#pragma once
+#include "internal.h"
+
+namespace vc {
+namespace fast {
+
+using C = float2;
+
+// A plan of two (R3 == 1) or three radix stages; stage s combines
+// sub-transforms of length NS_s with radix R_s (Stockham autosort).
+template <int R1_, int R2_, int R3_> struct Plan {
+  static constexpr int R1 = R1_, R2 = R2_, R3 = R3_;
+  static constexpr int L = R1 * R2 * R3;
+  static constexpr int NST = R3 > 1 ? 3 : 2;
+  static constexpr int RL = R3 > 1 ? R3 : R2;            // radix of the last stage
+  static constexpr int NSL = L / RL;                     // its sub-transform length
+};
+
+// v[r] *= w_r (conjugated for the inverse), w_r = tw[k (R-1) + r - 1]
+template <int R, bool INV>
+__device__ __forceinline__ void twiddle(C* v, const C* __restrict__ tw, int k) {
+  const C* w = tw + k * (R - 1);
+#pragma unroll
+  for (int r = 1; r < R; ++r) {
+    C ww = w[r - 1];
+    if (INV) ww.y = -ww.y;
+    v[r] = cmul(v[r], ww);
+  }
+}
+
+// One stage (radix R, sub-transform length NS) over TX interleaved lines of
+// length L; butterfly item = (j, c) with c = item % TX fastest, spread over
+// NT threads.  ld(c, pos) gives the input, st(c, pos, v) takes the output.
+// All inputs of a thread's butterflies are loaded before any is transformed,
+// so that a stage reading HBM keeps all of its loads in flight at once.
+template <int L, int R, int NS, int TX, int NT, bool INV, typename Ld, typename St>
+__device__ __forceinline__ void stage(const C* __restrict__ tw, Ld ld, St st) {
+  constexpr int NB = L / R, TOT = NB * TX, IT = (TOT + NT - 1) / NT;
+  C v[IT][R];
+#pragma unroll
+  for (int it = 0; it < IT; ++it) {
+    const int item = it * NT + (int)threadIdx.x;
+    if (TOT % NT == 0 || item < TOT) {
+      const int c = item % TX, j = item / TX;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[it][r] = ld(c, j + r * NB);
+    }
+  }
+#pragma unroll
+  for (int it = 0; it < IT; ++it) {
+    const int item = it * NT + (int)threadIdx.x;
+    if (TOT % NT == 0 || item < TOT) {
+      const int c = item % TX, j = item / TX, k = j % NS;
+      if (NS > 1) twiddle<R, INV>(v[it], tw, k);
+      dft<R, C>(v[it], INV);
+      const int base = (j - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) st(c, base + r * NS, v[it][r]);
+    }
+  }
+}
+
+// The same stage in place on buf (element (pos, c) at pos * PT + c, pitch
+// PT >= TX): all inputs of a thread's butterflies are read, the block
+// synchronises, the outputs are written, and the block synchronises again.
+template <int L, int R, int NS, int TX, int NT, bool INV, int PT = TX>
+__device__ __forceinline__ void stage_inplace(C* buf, const C* __restrict__ tw) {
+  constexpr int NB = L / R, TOT = NB * TX, IT = (TOT + NT - 1) / NT;
+  C v[IT][R];
+#pragma unroll
+  for (int it = 0; it < IT; ++it) {
+    const int item = it * NT + (int)threadIdx.x;
+    if (TOT % NT == 0 || item < TOT) {
+      const int c = item % TX, j = item / TX;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[it][r] = buf[(j + r * NB) * PT + c];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < IT; ++it) {
+    const int item = it * NT + (int)threadIdx.x;
+    if (TOT % NT == 0 || item < TOT) {
+      const int c = item % TX, j = item / TX, k = j % NS;
+      if (NS > 1) twiddle<R, INV>(v[it], tw, k);
+      dft<R, C>(v[it], INV);
+      const int base = (j - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[(base + r * NS) * PT + c] = v[it][r];
+    }
+  }
+  __syncthreads();
+}
+
+// A whole transform of TX interleaved lines held in buf, every stage in
+// place (twiddle tables of the plan's stages at tw + off[s]).
+template <typename P, int TX, int NT, bool INV, int PT = TX>
+__device__ __forceinline__ void transform_inplace(C* buf, const C* __restrict__ tw, int off2, int off3) {
+  stage_inplace<P::L, P::R1, 1, TX, NT, INV, PT>(buf, tw);
+  stage_inplace<P::L, P::R2, P::R1, TX, NT, INV, PT>(buf, tw + off2);
+  if constexpr (P::NST == 3) stage_inplace<P::L, P::R3, P::R1 * P::R2, TX, NT, INV, PT>(buf, tw + off3);
+}
+
+// copy n complex values to shared memory (caller synchronises)
+template <int NT>
+__device__ __forceinline__ void load_table(C* dst, const C* __restrict__ src, int n) {
+  for (int i = threadIdx.x; i < n; i += NT) dst[i] = src[i];
+}
+
+}  // namespace fast
+
+// ---- dispatch (fast_*.cu): each returns VOXCAP_ERR_UNSUPPORTED when no
+// compiled plan matches the handle's lengths, so that the caller falls back
+// to the generic passes.
+bool fast_plan_ok(const Plan1D<float2>& p);
+int fast_ypass(const Handle& h, bool inv, int G, const float2* in, float2* out, int64_t in_bstride,
+               int64_t out_bstride, int B, int variant, cudaStream_t st);
+bool fast_z_ok(const Handle& h);
+int fast_zpass(const Handle& h, float2* data, int B, cudaStream_t st);
+// forward x passes (panel scatter + R2C along x; C2R along x + panel gather)
+bool fast_x_ok(const Handle& h);
+int fast_xfwd(const Handle& h, const float* x, float2* out, int nrhs, cudaStream_t st);
+int fast_xinv(const Handle& h, const float2* in, const float* x, float* y, int nrhs, cudaStream_t st);
+
+}  // namespace vc

@@ -1,0 +1,232 @@
+// x passes of the forward FP32 product (Eqs. 9-11) on compiled plans.
+//
+// xfwd: the panel charges of each face row are scattered straight from the
+// panel list (every row of the canonical order is one contiguous run of
+// conductor panels and one of dielectric panels) onto a zeroed line in
+// shared memory -- two real rows per complex line --, the line is
+// transformed along x, and the half spectra of the two rows are split out,
+// given the half-voxel phase of the x grid and written to HBM (row-
+// contiguous, coalesced).
+// xinv: the potential and field half spectra of an output row are read
+// (coalesced), extended to the full Hermitian line as potential + i field,
+// transformed back, and gathered at the row's panels: a conductor row takes
+// the potential, a dielectric row I' x + the field (Eq. 4).
+// NL lines share one shared-memory buffer with a pitch of NL + 1 complex
+// values, so that reads along x by consecutive lanes avoid bank conflicts.
+#include "fast.cuh"
+
+namespace vc {
+
+namespace {
+
+using fast::C;
+
+struct XArgs {
+  Geom g;
+  int nrhs;
+  int64_t N;
+  const int32_t* rstart;
+  const int32_t* px;
+  const float* idiag;
+  int64_t R;             // face rows per (structure, kind): 3 Lz Ly
+};
+
+template <int R1, int R2, int R3, int NL, int NT>
+__global__ void __launch_bounds__(NT) k_xfwd_fast(XArgs a, const float* __restrict__ x, C* __restrict__ out,
+                                                  const C* __restrict__ stw, int twn, int off2, int off3,
+                                                  const C* __restrict__ phx) {
+  using P = fast::Plan<R1, R2, R3>;
+  constexpr int L = P::L, H = L / 2 + 1, PT = NL + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  C* tws = buf + L * PT;
+  fast::load_table<NT>(tws, stw, twn);
+  const Geom& g = a.g;
+  const int z = blockIdx.y;
+  const int bg = blockIdx.z;                 // b * 3 + grid
+  const int grid = bg % 3, b = bg / 3;
+  const int s = b / a.nrhs, r = b % a.nrhs;
+  const int nlines = (g.Ly + 1) / 2;         // two rows per complex line
+  const int l0 = blockIdx.x * NL;
+  const float* xr = x + (int64_t)r * a.N;
+  for (int i = threadIdx.x; i < L * PT; i += NT) buf[i] = mk<C>(0.f, 0.f);
+  __syncthreads();
+  // scatter: one warp per row (2 NL rows), lanes over the row's panels
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* fb = reinterpret_cast<float*>(buf);
+  for (int rr = warp; rr < 2 * NL; rr += NT / 32) {
+    const int l = rr >> 1, part = rr & 1;
+    const int y = 2 * (l0 + l) + part;
+    if (l0 + l >= nlines || y >= g.Ly) continue;
+    const int64_t row = ((int64_t)grid * g.Lz + z) * g.Ly + y;
+#pragma unroll
+    for (int kind = 0; kind < 2; ++kind) {
+      const int64_t q = (2 * (int64_t)s + kind) * a.R + row;
+      const int p1 = a.rstart[q + 1];
+      for (int p = a.rstart[q] + lane; p < p1; p += 32) fb[2 * (a.px[p] * PT + l) + part] = xr[p];
+    }
+  }
+  __syncthreads();
+  fast::transform_inplace<P, NL, NT, false, PT>(buf, tws, off2, off3);
+  // split the two rows' half spectra, phase of the x grid, store
+  for (int t = threadIdx.x; t < H * NL; t += NT) {
+    const int l = t / H, k = t - l * H;
+    if (l0 + l >= nlines) continue;
+    const C zk = buf[k * PT + l];
+    const C zc = cconj(buf[((L - k) % L) * PT + l]);
+    C A = cscale(cadd(zk, zc), 0.5f);
+    C B = cscale(cmul_mi(csub(zk, zc)), 0.5f);
+    if (grid == 0) {
+      const C ph = phx[k];
+      A = cmul(A, ph);
+      B = cmul(B, ph);
+    }
+    const int y0 = 2 * (l0 + l);
+    C* o = out + (((int64_t)b * 3 + grid) * g.Lz + z) * ((int64_t)g.Ly * H);
+    o[(int64_t)y0 * H + k] = A;
+    if (y0 + 1 < g.Ly) o[(int64_t)(y0 + 1) * H + k] = B;
+  }
+}
+
+template <int R1, int R2, int R3, int NL, int NT>
+__global__ void __launch_bounds__(NT) k_xinv_fast(XArgs a, const C* __restrict__ in, const float* __restrict__ x,
+                                                  float* __restrict__ y, const C* __restrict__ stw, int twn,
+                                                  int off2, int off3, const C* __restrict__ phx) {
+  using P = fast::Plan<R1, R2, R3>;
+  constexpr int L = P::L, H = L / 2 + 1, PT = NL + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  C* tws = buf + L * PT;
+  fast::load_table<NT>(tws, stw, twn);
+  const Geom& g = a.g;
+  const int z = blockIdx.y;
+  const int bo = blockIdx.z;                 // b * 3 + orientation
+  const int al = bo % 3, b = bo / 3;
+  const int s = b / a.nrhs, r = b % a.nrhs;
+  const int l0 = blockIdx.x * NL;
+  const int64_t plane = (int64_t)g.Ly * H;
+  const C* srcA = in + (((int64_t)b * 6 + al) * g.Lz + z) * plane;        // potential
+  const C* srcB = in + (((int64_t)b * 6 + 3 + al) * g.Lz + z) * plane;    // field
+  // Hermitian extension of potential + i field, lanes along x
+  for (int t = threadIdx.x; t < L * NL; t += NT) {
+    const int l = t / L, k = t - l * L;
+    C v = mk<C>(0.f, 0.f);
+    if (l0 + l < g.Ly) {
+      const int kk = k <= L / 2 ? k : L - k;
+      const int64_t ro = (int64_t)(l0 + l) * H + kk;
+      C A = srcA[ro];
+      C B = srcB[ro];
+      if (al == 0) {
+        const C ph = cconj(phx[kk]);
+        A = cmul(A, ph);
+        B = cmul(B, ph);
+      }
+      if (k > L / 2) {
+        A = cconj(A);
+        B = cconj(B);
+      }
+      v = cadd(A, cmul_pi(B));
+    }
+    buf[k * PT + l] = v;
+  }
+  __syncthreads();
+  fast::transform_inplace<P, NL, NT, true, PT>(buf, tws, off2, off3);
+  // gather at the panels of each row: one warp per row
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float* xr = x + (int64_t)r * a.N;
+  float* yr = y + (int64_t)r * a.N;
+  for (int l = warp; l < NL; l += NT / 32) {
+    const int yy = l0 + l;
+    if (yy >= g.Ly) continue;
+    const int64_t row = ((int64_t)al * g.Lz + z) * g.Ly + yy;
+    const int64_t qc = (2 * (int64_t)s) * a.R + row;
+    const int64_t qd = (2 * (int64_t)s + 1) * a.R + row;
+    for (int p = a.rstart[qc] + lane, p1 = a.rstart[qc + 1]; p < p1; p += 32)
+      yr[p] = buf[a.px[p] * PT + l].x;
+    for (int p = a.rstart[qd] + lane, p1 = a.rstart[qd + 1]; p < p1; p += 32)
+      yr[p] = a.idiag[p] * xr[p] + buf[a.px[p] * PT + l].y;
+  }
+}
+
+XArgs xargs(const Handle& h, int nrhs) {
+  XArgs a;
+  a.g = h.g;
+  a.nrhs = nrhs;
+  a.N = h.pan.N;
+  a.rstart = h.pan.rstart.p;
+  a.px = h.pan.px.p;
+  a.idiag = h.pan.idiag_f.p;
+  a.R = 3 * (int64_t)h.g.Lz * h.g.Ly;
+  return a;
+}
+
+template <int R1, int R2, int R3, int NL, int NT>
+int launch_xfwd(const Handle& h, const float* x, C* out, int nrhs, cudaStream_t st) {
+  const Geom& g = h.g;
+  const Plan1D<float2>& p = h.pf[0];
+  constexpr int L = R1 * R2 * R3;
+  const size_t sm = ((size_t)L * (NL + 1) + p.twn) * sizeof(C);
+  auto kern = k_xfwd_fast<R1, R2, R3, NL, NT>;
+  VC_TRY(set_smem(kern, sm));
+  const int nlines = (g.Ly + 1) / 2;
+  const int B = h.pan.S * nrhs;
+  dim3 grid((nlines + NL - 1) / NL, g.Lz, B * 3);
+  kern<<<grid, NT, sm, st>>>(xargs(h, nrhs), x, out, p.stw, p.twn, p.twoff[1], p.nst >= 3 ? p.twoff[2] : 0,
+                             h.phf[0]);
+  ::vc::note_launch();
+  VC_CUDA(cudaGetLastError());
+  return VOXCAP_OK;
+}
+
+template <int R1, int R2, int R3, int NL, int NT>
+int launch_xinv(const Handle& h, const C* in, const float* x, float* y, int nrhs, cudaStream_t st) {
+  const Geom& g = h.g;
+  const Plan1D<float2>& p = h.pf[0];
+  constexpr int L = R1 * R2 * R3;
+  const size_t sm = ((size_t)L * (NL + 1) + p.twn) * sizeof(C);
+  auto kern = k_xinv_fast<R1, R2, R3, NL, NT>;
+  VC_TRY(set_smem(kern, sm));
+  const int B = h.pan.S * nrhs;
+  dim3 grid((g.Ly + NL - 1) / NL, g.Lz, B * 3);
+  kern<<<grid, NT, sm, st>>>(xargs(h, nrhs), in, x, y, p.stw, p.twn, p.twoff[1], p.nst >= 3 ? p.twoff[2] : 0,
+                             h.phf[0]);
+  ::vc::note_launch();
+  VC_CUDA(cudaGetLastError());
+  return VOXCAP_OK;
+}
+
+// plan -> instantiation; fwd selects xfwd or xinv
+template <bool FWD>
+int dispatch_x(const Handle& h, const float* x, const C* in, C* out, float* y, int nrhs, cudaStream_t st) {
+  const Plan1D<float2>& p = h.pf[0];
+  const int* r = p.radix;
+#define VC_X(A, B_, C_, NL, NT)                                                                  \
+  return FWD ? launch_xfwd<A, B_, C_, NL, NT>(h, x, out, nrhs, st)                               \
+             : launch_xinv<A, B_, C_, NL, NT>(h, in, x, y, nrhs, st)
+  if (p.nst == 2) {
+    if (r[0] == 4 && r[1] == 9) VC_X(4, 9, 1, 16, 128);
+    if (r[0] == 8 && r[1] == 9) VC_X(8, 9, 1, 16, 128);
+    if (r[0] == 16 && r[1] == 9) VC_X(16, 9, 1, 16, 256);
+  } else if (p.nst == 3 && r[2] == 9) {
+    if (r[0] == 8 && r[1] == 4) VC_X(8, 4, 9, 16, 256);
+    if (r[0] == 16 && r[1] == 4) VC_X(16, 4, 9, 16, 256);
+    if (r[0] == 16 && r[1] == 8) VC_X(16, 8, 9, 8, 256);
+  }
+#undef VC_X
+  set_error("no compiled x-pass plan for this length");
+  return VOXCAP_ERR_UNSUPPORTED;
+}
+
+}  // namespace
+
+bool fast_x_ok(const Handle& h) { return fast_plan_ok(h.pf[0]); }
+
+int fast_xfwd(const Handle& h, const float* x, float2* out, int nrhs, cudaStream_t st) {
+  return dispatch_x<true>(h, x, nullptr, out, nullptr, nrhs, st);
+}
+
+int fast_xinv(const Handle& h, const float2* in, const float* x, float* y, int nrhs, cudaStream_t st) {
+  return dispatch_x<false>(h, x, in, nullptr, y, nrhs, st);
+}
+
+}  // namespace vc

@@ -1,0 +1,119 @@
+// y passes of the FP32 products (Eqs. 9-11) on compiled plans: the forward
+// transform along y of the x-transformed charge planes (zero rows y >= N_y+1
+// are the padding and are not read) and the inverse transform back to the
+// N_y+1 rows the panels need, with the half-voxel phase of the y grids.
+//
+// A CTA transforms TX = 16 consecutive kx columns (128-byte row segments) of
+// one z plane of one grid: the first stage reads HBM into registers and
+// writes the one shared-memory buffer, a middle stage runs in place, and the
+// last stage writes HBM from registers.
+#include "fast.cuh"
+
+namespace vc {
+
+namespace {
+
+using fast::C;
+
+template <bool INV, int R1, int R2, int R3, int TX, int NT>
+__global__ void __launch_bounds__(NT) k_ypass_fast(Geom g, int G, const C* __restrict__ in, C* __restrict__ out,
+                                                   int64_t in_bstride, int64_t out_bstride,
+                                                   const C* __restrict__ stw, int twn, int off2, int off3,
+                                                   const C* __restrict__ phy) {
+  using P = fast::Plan<R1, R2, R3>;
+  constexpr int L = P::L;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  C* tws = buf + L * TX;
+  fast::load_table<NT>(tws, stw, twn);
+  const int H = g.Hx;
+  const int k0 = blockIdx.x * TX;
+  const int z = blockIdx.y;
+  const int bg = blockIdx.z;
+  const int grid = bg % G, b = bg / G;
+  const bool phase = (grid % 3) == 1;
+  const int Lin = INV ? L : g.Ly;
+  const int Lout = INV ? g.Ly : L;
+  const int ncol = min(TX, H - k0);
+  const C* src = in + (int64_t)b * in_bstride + ((int64_t)grid * g.Lz + z) * ((int64_t)Lin * H) + k0;
+  C* dst = out + (int64_t)b * out_bstride + ((int64_t)grid * g.Lz + z) * ((int64_t)Lout * H) + k0;
+  __syncthreads();
+  // first stage: HBM -> registers -> buffer
+  fast::stage<L, R1, 1, TX, NT, INV>(
+      tws,
+      [&](int c, int y) -> C {
+        C v = mk<C>(0.f, 0.f);
+        if (c < ncol && y < Lin) {
+          v = src[(int64_t)y * H + c];
+          if (INV && phase) v = cmul(v, cconj(phy[y]));
+        }
+        return v;
+      },
+      [&](int c, int pos, C v) { buf[pos * TX + c] = v; });
+  __syncthreads();
+  if constexpr (P::NST == 3) fast::stage_inplace<L, R2, R1, TX, NT, INV>(buf, tws + off2);
+  // last stage: buffer -> registers -> HBM
+  fast::stage<L, P::RL, P::NSL, TX, NT, INV>(
+      tws + (P::NST == 3 ? off3 : off2), [&](int c, int pos) -> C { return buf[pos * TX + c]; },
+      [&](int c, int y, C v) {
+        if (c < ncol && y < Lout) {
+          if (!INV && phase) v = cmul(v, phy[y]);
+          dst[(int64_t)y * H + c] = v;
+        }
+      });
+}
+
+template <bool INV, int R1, int R2, int R3, int TX, int NT>
+int launch_y(const Handle& h, int G, const C* in, C* out, int64_t ibs, int64_t obs, int B, cudaStream_t st) {
+  const Geom& g = h.g;
+  const Plan1D<float2>& p = h.pf[1];
+  constexpr int L = R1 * R2 * R3;
+  const size_t sm = ((size_t)L * TX + p.twn) * sizeof(C);
+  auto kern = k_ypass_fast<INV, R1, R2, R3, TX, NT>;
+  VC_TRY(set_smem(kern, sm));
+  dim3 grid((g.Hx + TX - 1) / TX, g.Lz, B * G);
+  kern<<<grid, NT, sm, st>>>(g, G, in, out, ibs, obs, p.stw, p.twn, p.twoff[1], p.nst >= 3 ? p.twoff[2] : 0,
+                             h.phf[1]);
+  ::vc::note_launch();
+  VC_CUDA(cudaGetLastError());
+  return VOXCAP_OK;
+}
+
+template <bool INV>
+int dispatch_y(const Handle& h, int G, const C* in, C* out, int64_t ibs, int64_t obs, int B, int variant,
+               cudaStream_t st) {
+  const Plan1D<float2>& p = h.pf[1];
+  const int* r = p.radix;
+  // threads: the first stage's butterflies at once where that fits in a block
+  if (p.nst == 2) {
+    if (r[0] == 4 && r[1] == 9) return launch_y<INV, 4, 9, 1, 16, 144>(h, G, in, out, ibs, obs, B, st);
+    if (r[0] == 8 && r[1] == 9) return launch_y<INV, 8, 9, 1, 16, 144>(h, G, in, out, ibs, obs, B, st);
+    if (r[0] == 16 && r[1] == 9) return launch_y<INV, 16, 9, 1, 16, 144>(h, G, in, out, ibs, obs, B, st);
+  } else if (p.nst == 3 && r[2] == 9) {
+    if (r[0] == 8 && r[1] == 4) return launch_y<INV, 8, 4, 9, 16, 288>(h, G, in, out, ibs, obs, B, st);
+    if (r[0] == 16 && r[1] == 4) return launch_y<INV, 16, 4, 9, 16, 288>(h, G, in, out, ibs, obs, B, st);
+    if (r[0] == 16 && r[1] == 8) {
+      if (variant == 1) return launch_y<INV, 16, 8, 9, 8, 288>(h, G, in, out, ibs, obs, B, st);
+      return launch_y<INV, 16, 8, 9, 16, 576>(h, G, in, out, ibs, obs, B, st);
+    }
+  }
+  set_error("no compiled y-pass plan for this length");
+  return VOXCAP_ERR_UNSUPPORTED;
+}
+
+}  // namespace
+
+bool fast_plan_ok(const Plan1D<float2>& p) {
+  const int* r = p.radix;
+  if (p.nst == 2) return r[1] == 9 && (r[0] == 4 || r[0] == 8 || r[0] == 16);
+  if (p.nst == 3) return r[2] == 9 && ((r[0] == 8 && r[1] == 4) || (r[0] == 16 && (r[1] == 4 || r[1] == 8)));
+  return false;
+}
+
+int fast_ypass(const Handle& h, bool inv, int G, const float2* in, float2* out, int64_t in_bstride,
+               int64_t out_bstride, int B, int variant, cudaStream_t st) {
+  if (inv) return dispatch_y<true>(h, G, in, out, in_bstride, out_bstride, B, variant, st);
+  return dispatch_y<false>(h, G, in, out, in_bstride, out_bstride, B, variant, st);
+}
+
+}  // namespace vc

@@ -92,6 +92,12 @@ struct Panels {
   DBuf<int32_t> la, lb;           // labels of the two sides (-1 outside)
   DBuf<int32_t> fmap;             // [S][3][Lz][Ly][Lx] -> global panel index or -1
   DBuf<int32_t> struct_of;        // [N] structure of each panel
+  // panels by face row: the panels of kind k on row (o, z, y) of structure s
+  // are [rstart[q], rstart[q + 1]) with q = (2 s + k) R + (o Lz + z) Ly + y,
+  // R = 3 Lz Ly (canonical order makes every row one contiguous run), and
+  // px[p] is the position of panel p along its row
+  DBuf<int32_t> rstart;
+  DBuf<int32_t> px;
 };
 
 // Pinned host ints the device writes directly (mapped), e.g. the per-step
@@ -184,6 +190,10 @@ struct Handle {
   int zvar = 0;                   // radix order of the z pass
   int ztx = -1;                   // log2 of its tile width, -1: heuristic
   int ytx[2] = {-1, -1};          // log2 of the forward / inverse y passes' tile widths (FP32)
+  // FP32 product kernels: 0 generic passes, 1 compiled-plan passes where the
+  // padded lengths have a compiled plan (fast_*.cu), -1 not chosen yet
+  int path = -1;
+  int yvar = 0;                   // variant of the compiled y pass (tile width)
   const double2* phd[3] = {nullptr, nullptr, nullptr};   // exp(+i pi k / M) per axis, k in [0, M)
   const float2* phf[3] = {nullptr, nullptr, nullptr};
   // Toeplitz tensors (FP64) and spectra
@@ -191,6 +201,8 @@ struct Handle {
   DBuf<double> toep[kNumKernels];
   DBuf<double> spec_d;            // [15][Oz][Oy][Hx] real, scaled by 1/(Mx My Mz)
   DBuf<float> spec_f;
+  DBuf<float> spec_v;             // [Oz][Oy][Hx][16] FP32: the 15 kernels of a frequency side by
+                                  // side (16th zero), read by the compiled z pass
   // MVM workspace
   int ws_batch = 0;
   DBuf<char> ws;                  // raw workspace

@@ -22,6 +22,9 @@
 // by row kind (6 input grids), the conjugated kernels and 3 output grids.
 // The z pass lives in zmac.cuh (one translation unit per precision and
 // direction); its variant and the y passes' tile widths are tuned at set-up.
+#include <type_traits>
+
+#include "fast.cuh"
 #include "internal.h"
 
 namespace vc {
@@ -293,8 +296,13 @@ int mvm(Handle& h, const T* x, T* y, int nrhs, bool adjoint, T* field_out, void*
   const int GI = adjoint ? 6 : 3, GO = adjoint ? 3 : 6;
   const int TB = 256;
   cudaStream_t st = h.stream;
+  // compiled-plan passes for FP32 where the lengths allow (path 1); the x
+  // passes of the transposed product and of the face-field output stay generic
+  const bool fast_x = std::is_same<T, float>::value && h.path == 1 && !adjoint && !field_out && fast_x_ok(h);
   // xfwd
-  {
+  if (fast_x) {
+    VC_TRY(fast_xfwd(h, reinterpret_cast<const float*>(x), reinterpret_cast<float2*>(bufX), nrhs, st));
+  } else {
     const int NL = smem_lines<T>(g.Mx, 1, 16);
     const int lines = adjoint ? g.Ly : (g.Ly + 1) / 2;
     dim3 grid((lines + NL - 1) / NL, g.Lz, B * 3);
@@ -312,13 +320,18 @@ int mvm(Handle& h, const T* x, T* y, int nrhs, bool adjoint, T* field_out, void*
     ::vc::note_launch();
     VC_CUDA(cudaGetLastError());
   }
+  const bool fast_y = std::is_same<T, float>::value && h.path == 1 && fast_plan_ok(h.pf[1]);
+  const bool fast_z = std::is_same<T, float>::value && h.path == 1 && !adjoint && fast_z_ok(h);
   // yfwd: bufX [B][GI] -> bufY [B][6] (first GI grids)
   // y tiles: the tuned widths for FP32 (4..16 columns), else the widest that fits
   const int TXdef = smem_lines<T>(g.My, 1, 16);
   const int TXf = (sizeof(T) == 4 && h.ytx[0] >= 0) ? (1 << h.ytx[0]) : TXdef;
   const int TXi = (sizeof(T) == 4 && h.ytx[1] >= 0) ? (1 << h.ytx[1]) : TXdef;
   const int ybufs = plan_of<T>(h, 1).nst >= 3 ? 2 : 1;
-  {
+  if (fast_y) {
+    VC_TRY(fast_ypass(h, false, GI, reinterpret_cast<const float2*>(bufX), reinterpret_cast<float2*>(bufY),
+                      (int64_t)GI * gX, (int64_t)6 * gY, B, h.yvar, st));
+  } else {
     const int TXy = TXf;
     const int TBy = TXy >= 16 ? 256 : 128;
     size_t sm = (ybufs * (size_t)g.My * TXy + plan_of<T>(h, 1).twn) * sizeof(C);
@@ -333,10 +346,14 @@ int mvm(Handle& h, const T* x, T* y, int nrhs, bool adjoint, T* field_out, void*
     VC_CUDA(cudaGetLastError());
   }
   // zmac
-  if (adjoint) VC_TRY((zmac_launch<T, true>(h, bufY, B, st)));
+  if (fast_z) VC_TRY(fast_zpass(h, reinterpret_cast<float2*>(bufY), B, st));
+  else if (adjoint) VC_TRY((zmac_launch<T, true>(h, bufY, B, st)));
   else VC_TRY((zmac_launch<T, false>(h, bufY, B, st)));
   // yinv: bufY [B][6] (first GO grids) -> bufX [B][GO]
-  {
+  if (fast_y) {
+    VC_TRY(fast_ypass(h, true, GO, reinterpret_cast<const float2*>(bufY), reinterpret_cast<float2*>(bufX),
+                      (int64_t)6 * gY, (int64_t)GO * gX, B, h.yvar, st));
+  } else {
     const int TXy = TXi;
     const int TBy = TXy >= 16 ? 256 : 128;
     size_t sm = (ybufs * (size_t)g.My * TXy + plan_of<T>(h, 1).twn) * sizeof(C);
@@ -351,7 +368,10 @@ int mvm(Handle& h, const T* x, T* y, int nrhs, bool adjoint, T* field_out, void*
     VC_CUDA(cudaGetLastError());
   }
   // xinv + gather
-  {
+  if (fast_x) {
+    VC_TRY(fast_xinv(h, reinterpret_cast<const float2*>(bufX), reinterpret_cast<const float*>(x),
+                     reinterpret_cast<float*>(y), nrhs, st));
+  } else {
     const int NL = smem_lines<T>(g.Mx, 1, 16);
     const int lines = adjoint ? (g.Ly + 1) / 2 : g.Ly;
     dim3 grid((lines + NL - 1) / NL, g.Lz, B * 3);

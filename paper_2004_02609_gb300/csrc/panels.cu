@@ -125,6 +125,22 @@ __global__ void k_scatter_panels(const int32_t* __restrict__ lab, int nx, int ny
   fmap[(((int64_t)s * 3 + o) * g.Lz + k) * ((int64_t)g.Ly * g.Lx) + (int64_t)j * g.Lx + i] = (int32_t)p;
 }
 
+// panels per face row, by structure and kind (see Panels::rstart)
+__global__ void k_row_count(int64_t N, const int8_t* __restrict__ orient, const int32_t* __restrict__ face,
+                            const int8_t* __restrict__ kind, const int32_t* __restrict__ struct_of, Geom g,
+                            int32_t* __restrict__ cnt, int32_t* __restrict__ px) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  const int o = orient[p];
+  const int Fx = o == 0 ? g.nx + 1 : g.nx, Fy = o == 1 ? g.ny + 1 : g.ny;
+  const int64_t f = face[p];
+  const int i = (int)(f % Fx), j = (int)((f / Fx) % Fy), k = (int)(f / ((int64_t)Fx * Fy));
+  const int64_t R = 3 * (int64_t)g.Lz * g.Ly;
+  const int64_t q = (2 * (int64_t)struct_of[p] + kind[p]) * R + ((int64_t)o * g.Lz + k) * g.Ly + j;
+  atomicAdd(cnt + q, 1);
+  px[p] = i;
+}
+
 int build_panels(Handle& h) {
   Geom& g = h.g;
   Panels& P = h.pan;
@@ -192,6 +208,26 @@ int build_panels(Handle& h) {
         P.off[s], s, g, P.orient.p, P.face.p, P.kind.p, P.owner.p, P.idiag.p, P.idiag_f.p,
         P.qscale.p, P.la.p, P.lb.p, P.fmap.p, P.struct_of.p); ::vc::note_launch();
     VC_CUDA(cudaGetLastError());
+  }
+  // face rows: counts by (structure, kind, row), then an exclusive scan; in
+  // canonical order the scan of a row is the index of its first panel
+  {
+    const int64_t nrows = 2 * (int64_t)S * 3 * g.Lz * g.Ly;
+    VC_CHECK(nrows < (int64_t)INT32_MAX, VOXCAP_ERR_ARG, "too many face rows");
+    VC_TRY(P.rstart.alloc((size_t)nrows + 1));
+    VC_TRY(P.px.alloc(N));
+    DBuf<int32_t> stmp;
+    VC_TRY(stmp.alloc((size_t)scan_tmp_elems(nrows + 1)));
+    VC_CUDA(cudaMemsetAsync(P.rstart.p, 0, sizeof(int32_t) * (size_t)(nrows + 1), h.stream));
+    if (ntot > 0) {
+      k_row_count<<<(unsigned)((ntot + TB - 1) / TB), TB, 0, h.stream>>>(ntot, P.orient.p, P.face.p, P.kind.p,
+                                                                       P.struct_of.p, g, P.rstart.p, P.px.p);
+      ::vc::note_launch();
+      VC_CUDA(cudaGetLastError());
+    }
+    int64_t tot = 0;
+    VC_TRY(exclusive_scan_i32(P.rstart.p, nrows + 1, stmp.p, &tot, h.stream));
+    VC_CHECK(tot == ntot, VOXCAP_ERR_CUDA, "face-row counts do not add up to the panel count");
   }
   // conductors per structure: largest owner + 1 over the structure's labels
   P.m.assign(S, 0);

@@ -15,6 +15,8 @@
 // arrives on an mbarrier, and the 4 warps read the accumulator lanes back
 // with tcgen05.ld and store FP64.  Every wait on the mbarrier is bounded:
 // on timeout the kernel records an error, releases its TMEM and returns.
+#include <algorithm>
+#include <cstring>
 #include <vector>
 
 #include "internal.h"
@@ -206,6 +208,25 @@ static int tc_gemm(const GemmArgs& g, int* err, cudaStream_t st) {
 
 // X[i + D1 (j + D2 k)] = sum S[a][b][c] U1[i][a] U2[j][b] U3[k][c]
 // S: r1 x r2 x r3 (c fastest); Un: Dn x rn row-major; all device pointers.
+// T1 (r1 r2 D3) and T2 (r1 D3 D2) are scratch; a timed-out MMA wait sets
+// *err.  Nothing is synchronised here.
+static int tucker_expand_async(const double* S, int r1, int r2, int r3, const double* U1, int D1,
+                               const double* U2, int D2, const double* U3, int D3, double* X, double* T1,
+                               double* T2, int* err, cudaStream_t st) {
+  GemmArgs g;
+  // T1[a][b][k] = sum_c S[a][b][c] U3[k][c]
+  g = GemmArgs{S, U3, T1, r1 * r2, D3, r3, 1, 0, r3, 1, 0, r3, 1, 0, D3, 1};
+  VC_TRY(tc_gemm(g, err, st));
+  // T2[a][k][j] = sum_b U2[j][b] T1[a][b][k]     (batch a)
+  g = GemmArgs{U2, T1, T2, D2, D3, r2, r1, 0, r2, 1, (int64_t)r2 * D3, 1, D3, (int64_t)D3 * D2, 1, D2};
+  VC_TRY(tc_gemm(g, err, st));
+  // X[i + D1 n] = sum_a U1[i][a] T2[a][n],  n = j + D2 k
+  g = GemmArgs{U1, T2, X, D1, D2 * D3, r1, 1, 0, r1, 1, 0, 1, (int64_t)D2 * D3, 0, 1, D1};
+  VC_TRY(tc_gemm(g, err, st));
+  return VOXCAP_OK;
+}
+
+// the same, standalone: its own scratch, one status read at the end
 int tucker_expand(const double* S, int r1, int r2, int r3, const double* U1, int D1, const double* U2,
                   int D2, const double* U3, int D3, double* X, cudaStream_t st) {
   DBuf<double> T1, T2;
@@ -214,16 +235,7 @@ int tucker_expand(const double* S, int r1, int r2, int r3, const double* U1, int
   VC_TRY(T2.alloc((size_t)r1 * D3 * D2));
   VC_TRY(err.alloc(1));
   VC_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
-  GemmArgs g;
-  // T1[a][b][k] = sum_c S[a][b][c] U3[k][c]
-  g = GemmArgs{S, U3, T1.p, r1 * r2, D3, r3, 1, 0, r3, 1, 0, r3, 1, 0, D3, 1};
-  VC_TRY(tc_gemm(g, err.p, st));
-  // T2[a][k][j] = sum_b U2[j][b] T1[a][b][k]     (batch a)
-  g = GemmArgs{U2, T1.p, T2.p, D2, D3, r2, r1, 0, r2, 1, (int64_t)r2 * D3, 1, D3, (int64_t)D3 * D2, 1, D2};
-  VC_TRY(tc_gemm(g, err.p, st));
-  // X[i + D1 n] = sum_a U1[i][a] T2[a][n],  n = j + D2 k
-  g = GemmArgs{U1, T2.p, X, D1, D2 * D3, r1, 1, 0, r1, 1, 0, 1, (int64_t)D2 * D3, 0, 1, D1};
-  VC_TRY(tc_gemm(g, err.p, st));
+  VC_TRY(tucker_expand_async(S, r1, r2, r3, U1, D1, U2, D2, U3, D3, X, T1.p, T2.p, err.p, st));
   int e = 0;
   VC_CUDA(cudaMemcpyAsync(&e, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
   VC_CUDA(cudaStreamSynchronize(st));
@@ -239,24 +251,26 @@ void toeplitz_dims(const Geom& g, int kk, int* d);
 // cropped to the grid's offset ranges, so only the small core is permuted
 // and the factor matrices are cut to their leading rows.
 int build_toeplitz_tucker(Handle& h, const voxcap_tucker& tk) {
+  // per tensor: canonical tensor t, grid axis of each of its modes
+  int tsel[kNumKernels], axm[kNumKernels][3];
+  size_t n1 = 1, n2 = 1, ncore = 1, nfac = 1;
   for (int kk = 0; kk < kNumKernels; ++kk) {
     int* d = h.tdims[kk];
     toeplitz_dims(h.g, kk, d);
     const int te = ker_test(kk), so = ker_src(kk);
-    int t, ax_of_mode[3];
+    int* ax_of_mode = axm[kk];
     if (te == so) {
-      t = kk >= 6 ? 1 : 0;
+      tsel[kk] = kk >= 6 ? 1 : 0;
       ax_of_mode[0] = te;
       ax_of_mode[1] = te == 0 ? 1 : 0;
       ax_of_mode[2] = te == 2 ? 1 : 2;
     } else {
-      t = kk >= 6 ? 3 : 2;
+      tsel[kk] = kk >= 6 ? 3 : 2;
       ax_of_mode[0] = te;
       ax_of_mode[1] = so;
       ax_of_mode[2] = 3 - te - so;
     }
-    int mode_of_ax[3];
-    for (int m = 0; m < 3; ++m) mode_of_ax[ax_of_mode[m]] = m;
+    const int t = tsel[kk];
     for (int m = 0; m < 3; ++m) {
       VC_CHECK(tk.dims[t][m] >= d[ax_of_mode[m]], VOXCAP_ERR_ARG,
                "Tucker tensor " + std::to_string(t) + " mode " + std::to_string(m) + " has " +
@@ -264,9 +278,35 @@ int build_toeplitz_tucker(Handle& h, const voxcap_tucker& tk) {
       VC_CHECK(tk.ranks[t][m] > 0 && tk.factor[t][m] != nullptr, VOXCAP_ERR_ARG, "bad Tucker factor");
     }
     VC_CHECK(tk.core[t] != nullptr, VOXCAP_ERR_ARG, "NULL Tucker core");
+    int mode_of_ax[3];
+    for (int m = 0; m < 3; ++m) mode_of_ax[ax_of_mode[m]] = m;
+    const int* r = tk.ranks[t];
+    const size_t rx = r[mode_of_ax[0]], ry = r[mode_of_ax[1]], rz = r[mode_of_ax[2]];
+    n1 = std::max(n1, rx * ry * (size_t)d[2]);
+    n2 = std::max(n2, rx * (size_t)d[2] * d[1]);
+    ncore = std::max(ncore, rx * ry * rz);
+    nfac = std::max(nfac, (size_t)d[0] * rx + (size_t)d[1] * ry + (size_t)d[2] * rz);
+  }
+  // scratch shared by the 15 restorations (stream-ordered), one status word
+  DBuf<double> T1, T2, dcore, dfac;
+  DBuf<int> err;
+  VC_TRY(T1.alloc(n1));
+  VC_TRY(T2.alloc(n2));
+  VC_TRY(err.alloc(1));
+  VC_TRY(dcore.alloc(ncore * kNumKernels));
+  VC_TRY(dfac.alloc(nfac * kNumKernels));
+  VC_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), h.stream));
+  std::vector<double> core(ncore * kNumKernels);
+  std::vector<double> fac(nfac * kNumKernels);
+  for (int kk = 0; kk < kNumKernels; ++kk) {
+    const int t = tsel[kk];
+    const int* d = h.tdims[kk];
+    int mode_of_ax[3];
+    for (int m = 0; m < 3; ++m) mode_of_ax[axm[kk][m]] = m;
     const int* r = tk.ranks[t];
     const int rx = r[mode_of_ax[0]], ry = r[mode_of_ax[1]], rz = r[mode_of_ax[2]];
-    std::vector<double> core((size_t)rx * ry * rz);
+    // the core with its modes permuted to (x, y, z) grid axes
+    double* cp = core.data() + ncore * kk;
     for (int p = 0; p < rx; ++p)
       for (int q = 0; q < ry; ++q)
         for (int s = 0; s < rz; ++s) {
@@ -274,21 +314,40 @@ int build_toeplitz_tucker(Handle& h, const voxcap_tucker& tk) {
           idx[mode_of_ax[0]] = p;
           idx[mode_of_ax[1]] = q;
           idx[mode_of_ax[2]] = s;
-          core[((size_t)p * ry + q) * rz + s] = tk.core[t][((size_t)idx[0] * r[1] + idx[1]) * r[2] + idx[2]];
+          cp[((size_t)p * ry + q) * rz + s] = tk.core[t][((size_t)idx[0] * r[1] + idx[1]) * r[2] + idx[2]];
         }
-    DBuf<double> dcore, du[3];
-    VC_TRY(dcore.alloc(core.size()));
-    VC_CUDA(cudaMemcpyAsync(dcore.p, core.data(), sizeof(double) * core.size(), cudaMemcpyHostToDevice, h.stream));
+    // the factors' leading rows (the crop to the grid)
+    double* fp = fac.data() + nfac * kk;
+    size_t o = 0;
     for (int ax = 0; ax < 3; ++ax) {
       const int m = mode_of_ax[ax];
       const size_t n = (size_t)d[ax] * r[m];
-      VC_TRY(du[ax].alloc(n));
-      VC_CUDA(cudaMemcpyAsync(du[ax].p, tk.factor[t][m], sizeof(double) * n, cudaMemcpyHostToDevice, h.stream));
+      std::memcpy(fp + o, tk.factor[t][m], sizeof(double) * n);
+      o += n;
     }
-    VC_TRY(h.toep[kk].alloc((size_t)d[0] * d[1] * d[2]));
-    VC_TRY(tucker_expand(dcore.p, rx, ry, rz, du[0].p, d[0], du[1].p, d[1], du[2].p, d[2], h.toep[kk].p,
-                         h.stream));
   }
+  // two uploads, then the 15 expansions back to back
+  VC_CUDA(cudaMemcpyAsync(dcore.p, core.data(), sizeof(double) * core.size(), cudaMemcpyHostToDevice, h.stream));
+  VC_CUDA(cudaMemcpyAsync(dfac.p, fac.data(), sizeof(double) * fac.size(), cudaMemcpyHostToDevice, h.stream));
+  for (int kk = 0; kk < kNumKernels; ++kk) {
+    const int t = tsel[kk];
+    const int* d = h.tdims[kk];
+    int mode_of_ax[3];
+    for (int m = 0; m < 3; ++m) mode_of_ax[axm[kk][m]] = m;
+    const int* r = tk.ranks[t];
+    const int rx = r[mode_of_ax[0]], ry = r[mode_of_ax[1]], rz = r[mode_of_ax[2]];
+    const double* fp = dfac.p + nfac * kk;
+    VC_TRY(h.toep[kk].alloc((size_t)d[0] * d[1] * d[2]));
+    VC_TRY(tucker_expand_async(dcore.p + ncore * kk, rx, ry, rz, fp, d[0], fp + (size_t)d[0] * rx, d[1],
+                               fp + (size_t)d[0] * rx + (size_t)d[1] * ry, d[2], h.toep[kk].p, T1.p, T2.p, err.p,
+                               h.stream));
+  }
+  // one status read for the whole restoration: after a timed-out wait the
+  // status is the only result to trust, and the set-up fails
+  int e = 0;
+  VC_CUDA(cudaMemcpyAsync(&e, err.p, sizeof(int), cudaMemcpyDeviceToHost, h.stream));
+  VC_CUDA(cudaStreamSynchronize(h.stream));
+  VC_CHECK(e == 0, VOXCAP_ERR_CUDA, "tensor-core Tucker expansion timed out waiting for its MMAs");
   return VOXCAP_OK;
 }
 

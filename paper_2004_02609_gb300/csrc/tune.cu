@@ -1,7 +1,8 @@
 // Set-up-time autotuning of the product: the radix order of the z pass's
 // transform (largest radix <= 9 last, or smallest last) and its tile width
 // (8 or 16 columns), then the tile widths of the inverse and forward y passes
-// (4, 8 or the default), are timed on the handle's own FP32 products, all
+// (4, 8 or the default), then the compiled-plan passes where the padded
+// lengths have one, are timed on the handle's own FP32 products, all
 // conductor columns at once, and the fastest is kept.  The choice is cached
 // per device, grid and batch, so later set-ups of the same shape reuse it.
 #include <algorithm>
@@ -9,13 +10,14 @@
 #include <map>
 #include <mutex>
 
+#include "fast.cuh"
 #include "internal.h"
 
 namespace vc {
 
 namespace {
 std::mutex g_tune_mu;
-std::map<std::array<int, 8>, std::array<int, 4>> g_tune;
+std::map<std::array<int, 8>, std::array<int, 6>> g_tune;
 }  // namespace
 
 static int tune(Handle& h, bool use_cache) {
@@ -32,6 +34,8 @@ static int tune(Handle& h, bool use_cache) {
       h.ztx = it->second[1];
       h.ytx[0] = it->second[2];
       h.ytx[1] = it->second[3];
+      h.path = it->second[4];
+      h.yvar = it->second[5];
       return VOXCAP_OK;
     }
   }
@@ -62,6 +66,8 @@ static int tune(Handle& h, bool use_cache) {
     return VOXCAP_OK;
   };
   h.ytx[0] = h.ytx[1] = -1;
+  h.path = 0;
+  h.yvar = 0;
   float best_ms = 1e30f;
   int best_v = 0, best_tx = -1;
   for (int v = 0; v < h.nzvar; ++v)
@@ -93,8 +99,27 @@ static int tune(Handle& h, bool use_cache) {
     }
     h.ytx[which] = best_y;
   }
+  // then the compiled-plan passes, where the lengths have a plan (two tile
+  // widths for the longest y plan)
+  if (fast_plan_ok(h.pf[1]) || fast_z_ok(h) || fast_x_ok(h)) {
+    const bool two = h.pf[1].nst == 3 && h.pf[1].radix[0] == 16 && h.pf[1].radix[1] == 8;
+    int best_path = 0, best_var = 0;
+    for (int v = 0; v < (two ? 2 : 1); ++v) {
+      h.path = 1;
+      h.yvar = v;
+      float ms;
+      VC_TRY(time_products(&ms));
+      if (ms >= 0.0f && ms < best_ms) {
+        best_ms = ms;
+        best_path = 1;
+        best_var = v;
+      }
+    }
+    h.path = best_path;
+    h.yvar = best_var;
+  }
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tune[key] = {h.zvar, h.ztx, h.ytx[0], h.ytx[1]};
+  g_tune[key] = {h.zvar, h.ztx, h.ytx[0], h.ytx[1], h.path, h.yvar};
   return VOXCAP_OK;
 }
 

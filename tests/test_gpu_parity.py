@@ -251,6 +251,52 @@ def test_matvec_every_radix(shape):
     assert vc.set_product_tiles()[0] in (0, 1)
 
 
+def _blob(n, axis):
+    """A grid of n voxels along `axis` (2 or 3 across) holding a small
+    structure near one end: a 2-voxel conductor with a one-voxel dielectric
+    (eps_r 4) cap, in vacuum.  The padded length along `axis` is 2^a * 9 for
+    the n used below; every panel pair stays within a few voxels, where the
+    oracle's integrals are fast and accurate."""
+    shape = [3, 3, 3]
+    shape[axis] = n
+    nx, ny, nz = shape
+    lab = np.zeros((nz, ny, nx), np.int32)
+    sl = [slice(0, 2)] * 3
+    sl[2 - axis] = slice(1, 3)
+    lab[tuple(sl)] = 2
+    cap = list(sl)
+    cap[2 - axis] = slice(3, 4)
+    lab[tuple(cap)] = 1
+    return W.Workload(f"blob{n}_{'xyz'[axis]}", lab, np.array([-1, -1, 0], np.int32), np.array([1.0, 4.0, 1.0]))
+
+
+@pytest.mark.parametrize("n,axis", [(17, 2), (35, 2), (64, 2), (35, 1), (64, 1), (128, 1), (260, 1), (515, 1),
+                                    (17, 0), (64, 0), (128, 0), (260, 0), (515, 0)])
+def test_matvec_compiled_plans(n, axis):
+    """The compiled-plan FP32 passes (path 1) on every compiled length (x and
+    y: 36, 72, 144, 288, 576, 1152 with two or three radix stages; z: 36, 72,
+    144), forward (compiled x, y and z passes) and transposed (compiled y
+    passes),
+    against the dense oracle; and the generic passes (path 0) on the same
+    handle.  The full padded transforms run although the structure is small."""
+    import torch
+    w = _blob(n, axis)
+    vc = make(w)
+    M = vc.fft_lengths()[axis]
+    assert M in (36, 72, 144, 288, 576, 1152), M
+    ps, A = dense(w)
+    X = np.random.default_rng(11).standard_normal((2, ps.n))
+    x32 = torch.tensor(X, device="cuda", dtype=torch.float32)
+    for path in (1, 0):
+        assert vc.set_product_path(path) == path
+        f = vc.matvec(x32).cpu().numpy()
+        t = vc.matvec(x32, adjoint=True).cpu().numpy()
+        for r in range(2):
+            assert rel_l2(f[r], A @ X[r]) < 2e-6, (path, r)
+            assert rel_l2(t[r], A.T @ X[r]) < 2e-6, (path, r)
+    assert vc.set_product_path(-1) in (0, 1)
+
+
 def test_matvec_paper_padding_equals_smooth_padding():
     """Any padded length >= 2N+1 gives the same linear convolution (Appendix B):
     the paper's 2(N+1) and the smooth length agree to rounding."""
