@@ -371,6 +371,18 @@ int voxcap_set_product_tiles(voxcap_t* h, int z_order, int z_tile_log2, int y_fw
                              int* choice_out);
 
 /*
+ * voxcap_setup_times -- wall seconds of the phases of the handle's
+ * voxcap_setup (the paper reports its set-up stages the same way, Table V):
+ * seconds[0] input copies and FFT plans, [1] panels (Sec. II.A-B), [2] the
+ * block-Toeplitz tensors, generated (Eqs. 5-6) or restored from Tucker
+ * factors (Eq. 13), [3] circulant embedding and kernel spectra (Eqs. 11-12),
+ * [4] preconditioner (Eq. 14), [5] autotuning of the products (zero when the
+ * choice was cached).  seconds: host, 6 doubles.  Returns VOXCAP_ERR_ARG for
+ * NULL arguments.
+ */
+int voxcap_setup_times(const voxcap_t* h, double* seconds);
+
+/*
  * voxcap_set_product_path -- which kernels run the handle's FP32 products
  * (Eqs. 9-12; an implementation choice, same results to rounding):
  *  path 0   the generic passes (any padded length; the FP64 products always
@@ -380,9 +392,10 @@ int voxcap_set_product_tiles(voxcap_t* h, int z_order, int z_tile_log2, int y_fw
  *           144; forward z pass only), the generic passes elsewhere;
  *  path -1  re-run the set-up autotuner, which times both on this handle's
  *           own products and keeps the faster (cached per device, grid and
- *           batch).
+ *           batch);
+ *  path -2  change nothing (query).
  *  path_out (may be NULL) receives the path in force.  Returns
- * VOXCAP_ERR_ARG for a NULL handle or a path outside -1..1.  Not safe while
+ * VOXCAP_ERR_ARG for a NULL handle or a path outside -2..1.  Not safe while
  * another call on the same handle runs.
  */
 int voxcap_set_product_path(voxcap_t* h, int path, int* path_out);

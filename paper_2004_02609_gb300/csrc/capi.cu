@@ -104,17 +104,31 @@ static int setup_impl(const int32_t* labels, int nx, int ny, int nz, int n_struc
     set_error(std::string("copy of the inputs failed: ") + cudaGetErrorString(cudaGetLastError()));
     return fail(VOXCAP_ERR_CUDA);
   }
+  // phase wall times (the stream is drained at each mark)
+  auto tp = std::chrono::steady_clock::now();
+  auto mark = [&](int i) {
+    cudaStreamSynchronize(h.stream);
+    const auto t = std::chrono::steady_clock::now();
+    h.setup_s[i] = std::chrono::duration<double>(t - tp).count();
+    tp = t;
+  };
   if ((rc = build_fft_plans(h))) return fail(rc);
+  mark(0);
   if ((rc = build_panels(h))) return fail(rc);
+  mark(1);
   if (h.opts.tucker) {
     if ((rc = build_toeplitz_tucker(h, *h.opts.tucker))) return fail(rc);
   } else if ((rc = build_toeplitz(h))) {
     return fail(rc);
   }
   h.opts.tucker = nullptr;        // the caller's factors are not retained
+  mark(2);
   if ((rc = build_spectra(h))) return fail(rc);
+  mark(3);
   if ((rc = build_precond(h))) return fail(rc);
+  mark(4);
   if ((rc = tune_products(h))) return fail(rc);
+  mark(5);
   *out = v;
   return VOXCAP_OK;
 }
@@ -289,12 +303,20 @@ int voxcap_set_product_tiles(voxcap_t* hv, int z_order, int z_tile_log2, int y_f
   return VOXCAP_OK;
 }
 
+int voxcap_setup_times(const voxcap_t* hv, double* seconds) {
+  VC_CHECK(hv != nullptr && seconds != nullptr, VOXCAP_ERR_ARG, "NULL handle or output");
+  for (int i = 0; i < 6; ++i) seconds[i] = hv->h.setup_s[i];
+  return VOXCAP_OK;
+}
+
 int voxcap_set_product_path(voxcap_t* hv, int path, int* path_out) {
   VC_CHECK(hv != nullptr, VOXCAP_ERR_ARG, "NULL handle");
-  VC_CHECK(path >= -1 && path <= 1, VOXCAP_ERR_ARG, "path must be -1, 0 or 1");
+  VC_CHECK(path >= -2 && path <= 1, VOXCAP_ERR_ARG, "path must be -2, -1, 0 or 1");
   Handle& h = hv->h;
   set_alloc_stream(h.stream);
-  if (path < 0) {
+  if (path == -2) {
+    // query only
+  } else if (path < 0) {
     VC_TRY(retune_products(h));
   } else {
     h.path = path;

@@ -37,19 +37,53 @@ constexpr bool kflip(int kk, int a) {
                                : (a == ktest(kk) ? kk < 6 : a == ksrc(kk));
 }
 
-// kernel value kk of a frequency record in HBM (16 floats, kernels side by
-// side) with the fold signs of the frequency applied
-template <int KK>
-__device__ __forceinline__ float kval(const float* rec, float sy, float sz) {
-  float v = __ldg(rec + KK);
-  if constexpr (kflip(KK, 1)) v *= sy;
-  if constexpr (kflip(KK, 2)) v *= sz;
-  return v;
+// kernel block of output grid AL and source grid BE: potential (HALF 0:
+// P^{ab} xx yy zz xy xz yz, the symmetric pairs shared) or normal field
+// (HALF 1: E^{ab} xx yy zz xy xz yz yx zx zy)
+constexpr int kidx(int half, int al, int be) {
+  return half == 0 ? (al == be ? al : (al + be == 1 ? 3 : (al + be == 2 ? 4 : 5)))
+                   : (al == be ? 6 + al
+                               : (al == 0 ? (be == 1 ? 9 : 10) : (al == 1 ? (be == 2 ? 11 : 12) : (be == 0 ? 13 : 14))));
+}
+
+// One output grid AL of half HALF at the thread's RB frequencies: the 3 RB
+// kernel values (read together from the 64-byte records), the fold signs,
+// the sum over the 3 source grids, the output half-voxel phase of z grids,
+// the first inverse stage, and the store to the line buffer.
+template <int HALF, int AL, int RA, int RB, int NT, int TX, int LD>
+__device__ __forceinline__ void mac_out(const float* __restrict__ specv, const int* off, bool col_ok, float sy,
+                                        const C* S, int t, int j, int c, const C* ph, C* buf) {
+  constexpr int L = RA * RB;
+  constexpr int K0 = kidx(HALF, AL, 0), K1 = kidx(HALF, AL, 1), K2 = kidx(HALF, AL, 2);
+  float kv[RB][3];
+#pragma unroll
+  for (int r = 0; r < RB; ++r) {
+    kv[r][0] = col_ok ? __ldg(specv + off[r] + K0) : 0.f;
+    kv[r][1] = col_ok ? __ldg(specv + off[r] + K1) : 0.f;
+    kv[r][2] = col_ok ? __ldg(specv + off[r] + K2) : 0.f;
+  }
+  C o[RB];
+#pragma unroll
+  for (int r = 0; r < RB; ++r) {
+    const float sz = (j + r * RA) > L / 2 ? -1.f : 1.f;
+    const float k0 = kv[r][0] * (kflip(K0, 1) ? sy : 1.f) * (kflip(K0, 2) ? sz : 1.f);
+    const float k1 = kv[r][1] * (kflip(K1, 1) ? sy : 1.f) * (kflip(K1, 2) ? sz : 1.f);
+    const float k2 = kv[r][2] * (kflip(K2, 1) ? sy : 1.f) * (kflip(K2, 2) ? sz : 1.f);
+    const C Q0 = S[(0 * RB + r) * NT + t], Q1 = S[(1 * RB + r) * NT + t], Q2 = S[(2 * RB + r) * NT + t];
+    C acc;
+    acc.x = fmaf(Q0.x, k0, fmaf(Q1.x, k1, Q2.x * k2));
+    acc.y = fmaf(Q0.y, k0, fmaf(Q1.y, k1, Q2.y * k2));
+    o[r] = HALF == 0 ? acc : cmul_mi(acc);
+    if (AL == 2) o[r] = cmul(o[r], cconj(ph[j + r * RA]));
+  }
+  dft<RB, C>(o, true);                                   // first inverse stage (radix RB, no twiddles)
+#pragma unroll
+  for (int r = 0; r < RB; ++r) buf[(j * RB + r) * LD + AL * TX + c] = o[r];
 }
 
 template <int RA, int RB, int TX>
 __global__ void __launch_bounds__(RA * TX, 2) k_zpass_fast(Geom g, C* __restrict__ data,
-                                                          const float4* __restrict__ specv,
+                                                          const float* __restrict__ specv,
                                                           const C* __restrict__ twf, int twn_f, int offB,
                                                           const C* __restrict__ twv, int twn_v, int offA,
                                                           const C* __restrict__ phz, int nbatch) {
@@ -106,54 +140,35 @@ __global__ void __launch_bounds__(RA * TX, 2) k_zpass_fast(Geom g, C* __restrict
   }
   __syncthreads();                                      // the buffer takes the outputs now
 
-  // frequency records of the column: (kz folded, ky folded, kx)
+  // frequency records of the column: (kz folded, ky folded, kx); 32-bit
+  // offsets (the launch checks that the records fit) computed once
   const int64_t q = q0 + c;
   const int ky = col_ok ? (int)(q / H) : 0;
   const int kx = col_ok ? (int)(q - (int64_t)ky * H) : 0;
   const bool fy = ky > g.My / 2;
   const float sy = fy ? -1.f : 1.f;
-  const int64_t rec0 = (int64_t)(fy ? g.My - ky : ky) * H + kx;
-  const int64_t zrec = (int64_t)g.Oy * H;
+  const int rec0 = (fy ? g.My - ky : ky) * H + kx;
+  const int zrec = g.Oy * H;
+  int off[RB];
+#pragma unroll
+  for (int r = 0; r < RB; ++r) {
+    const int kz = j + r * RA;
+    off[r] = ((kz > L / 2 ? L - kz : kz) * zrec + rec0) * 16;
+  }
 
 #pragma unroll 1
   for (int half = 0; half < 2; ++half) {
     // potential outputs (half 0: kernels 0..5, Eq. 12 pairs shared) or
     // normal-field outputs (half 1: kernels 6..14, times -i), one output
-    // grid at a time
-#pragma unroll
-    for (int al = 0; al < 3; ++al) {
-      C o[RB];
-#pragma unroll
-      for (int r = 0; r < RB; ++r) {
-        const int kz = j + r * RA;
-        const bool fz = kz > L / 2;
-        const float sz = fz ? -1.f : 1.f;
-        const float* rec = reinterpret_cast<const float*>(specv) + ((int64_t)(fz ? L - kz : kz) * zrec + rec0) * 16;
-        float k0 = 0.f, k1 = 0.f, k2 = 0.f;
-        if (col_ok) {
-          if (half == 0) {       // P^{ab}: xx yy zz xy xz yz
-            if (al == 0) { k0 = kval<0>(rec, sy, sz); k1 = kval<3>(rec, sy, sz); k2 = kval<4>(rec, sy, sz); }
-            if (al == 1) { k0 = kval<3>(rec, sy, sz); k1 = kval<1>(rec, sy, sz); k2 = kval<5>(rec, sy, sz); }
-            if (al == 2) { k0 = kval<4>(rec, sy, sz); k1 = kval<5>(rec, sy, sz); k2 = kval<2>(rec, sy, sz); }
-          } else {               // E^{ab}: xx yy zz xy xz yz yx zx zy
-            if (al == 0) { k0 = kval<6>(rec, sy, sz); k1 = kval<9>(rec, sy, sz); k2 = kval<10>(rec, sy, sz); }
-            if (al == 1) { k0 = kval<12>(rec, sy, sz); k1 = kval<7>(rec, sy, sz); k2 = kval<11>(rec, sy, sz); }
-            if (al == 2) { k0 = kval<13>(rec, sy, sz); k1 = kval<14>(rec, sy, sz); k2 = kval<8>(rec, sy, sz); }
-          }
-        }
-        const C Q0 = S[(0 * RB + r) * NT + t], Q1 = S[(1 * RB + r) * NT + t], Q2 = S[(2 * RB + r) * NT + t];
-        C acc;
-        acc.x = fmaf(Q0.x, k0, fmaf(Q1.x, k1, Q2.x * k2));
-        acc.y = fmaf(Q0.y, k0, fmaf(Q1.y, k1, Q2.y * k2));
-        o[r] = half == 0 ? acc : cmul_mi(acc);
-      }
-      if (al == 2) {
-#pragma unroll
-        for (int r = 0; r < RB; ++r) o[r] = cmul(o[r], cconj(ph[j + r * RA]));
-      }
-      dft<RB, C>(o, true);                               // first inverse stage (radix RB, no twiddles)
-#pragma unroll
-      for (int r = 0; r < RB; ++r) buf[(j * RB + r) * LD + al * TX + c] = o[r];
+    // grid at a time; the 3 RB kernel values of a grid are loaded together
+    if (half == 0) {
+      mac_out<0, 0, RA, RB, NT, TX, LD>(specv, off, col_ok, sy, S, t, j, c, ph, buf);
+      mac_out<0, 1, RA, RB, NT, TX, LD>(specv, off, col_ok, sy, S, t, j, c, ph, buf);
+      mac_out<0, 2, RA, RB, NT, TX, LD>(specv, off, col_ok, sy, S, t, j, c, ph, buf);
+    } else {
+      mac_out<1, 0, RA, RB, NT, TX, LD>(specv, off, col_ok, sy, S, t, j, c, ph, buf);
+      mac_out<1, 1, RA, RB, NT, TX, LD>(specv, off, col_ok, sy, S, t, j, c, ph, buf);
+      mac_out<1, 2, RA, RB, NT, TX, LD>(specv, off, col_ok, sy, S, t, j, c, ph, buf);
     }
     __syncthreads();
     // ---- last inverse stage (radix RA), buffer -> HBM, planes z < Lz
@@ -177,10 +192,11 @@ int launch_z(const Handle& h, C* data, int B, cudaStream_t st) {
   const size_t sm = ((size_t)L * 3 * TX + (size_t)3 * RB * RA * TX + pz.twn + pv.twn + L) * sizeof(C);
   const int64_t cols = (int64_t)g.My * g.Hx;
   const int64_t tiles = (cols + TX - 1) / TX;
-  VC_CHECK(tiles * B < ((int64_t)1 << 31), VOXCAP_ERR_UNSUPPORTED, "grid too large for the z pass");
+  VC_CHECK(tiles * B < ((int64_t)1 << 31) && (int64_t)g.Hx * g.Oy * g.Oz * 16 < ((int64_t)1 << 31),
+           VOXCAP_ERR_UNSUPPORTED, "grid too large for the compiled z pass");
   auto kern = k_zpass_fast<RA, RB, TX>;
   VC_TRY(set_smem(kern, sm));
-  kern<<<(unsigned)(tiles * B), RA * TX, sm, st>>>(g, data, reinterpret_cast<const float4*>(h.spec_v.p), pz.stw,
+  kern<<<(unsigned)(tiles * B), RA * TX, sm, st>>>(g, data, h.spec_v.p, pz.stw,
                                                    pz.twn, pz.twoff[1], pv.stw, pv.twn, pv.twoff[1], h.phf[2], B);
   ::vc::note_launch();
   VC_CUDA(cudaGetLastError());

@@ -211,6 +211,7 @@ struct Handle {
   DBuf<double> rhs;               // last capacitance RHS
   bool have_rho = false;
   DBuf<char> solver_ws;
+  double setup_s[6] = {0, 0, 0, 0, 0, 0};   // wall seconds of the set-up phases (voxcap_setup_times)
   HostMap act_map;                // GMRES: [2][nrhs] active flags per step parity, then the
                                   // cycle-end read-back of iteration counts and flags [2][nrhs]
 };

@@ -30,7 +30,7 @@ SYMBOLS = ["voxcap_default_opts", "voxcap_last_error", "voxcap_setup", "voxcap_d
            "voxcap_capacitance", "voxcap_capacitance_grad", "voxcap_update_eps",
            "voxcap_entries", "voxcap_fft_length", "voxcap_toeplitz", "voxcap_launch_count",
            "voxcap_matvec_noalloc", "voxcap_tucker_expand", "voxcap_canonical_tensors",
-           "voxcap_set_product_tiles", "voxcap_set_product_path"]
+           "voxcap_set_product_tiles", "voxcap_setup_times", "voxcap_set_product_path"]
 
 
 class Tucker(ctypes.Structure):
@@ -96,6 +96,7 @@ def lib():
         L.voxcap_canonical_tensors.argtypes = [i32, vp, vp, vp, vp]
         L.voxcap_set_product_tiles.argtypes = [vp, i32, i32, i32, i32, P(i32)]
         L.voxcap_set_product_path.argtypes = [vp, i32, P(i32)]
+        L.voxcap_setup_times.argtypes = [vp, vp]
         L.voxcap_launch_count.argtypes = []
         L.voxcap_launch_count.restype = ctypes.c_int64
         _LIB = L
@@ -213,9 +214,17 @@ class VoxCap:
         _check(lib().voxcap_set_product_tiles(self._h, z_order, z_tile_log2, y_fwd_log2, y_inv_log2, out))
         return tuple(out)
 
+    def setup_times(self):
+        """Wall seconds of the set-up phases: plans, panels, Toeplitz tensors
+        (generated or Tucker-restored), spectra, preconditioner, tuning."""
+        out = np.zeros(6, np.float64)
+        _check(lib().voxcap_setup_times(self._h, out.ctypes.data))
+        return dict(zip(("plans", "panels", "toeplitz", "spectra", "precond", "tuning"), out.tolist()))
+
     def set_product_path(self, path=-1):
         """FP32 product kernels: 0 generic, 1 compiled radix plans where the
-        padded lengths have one, -1 re-tune; returns the path in force."""
+        padded lengths have one, -1 re-tune, -2 query; returns the path in
+        force."""
         out = ctypes.c_int()
         _check(lib().voxcap_set_product_path(self._h, int(path), ctypes.byref(out)))
         return out.value
