@@ -254,6 +254,7 @@ int voxcap_update_eps(voxcap_t* hv, const double* eps_r) {
              "eps_r must be positive and finite for dielectric labels");
   h.eps.assign(eps_r, eps_r + h.nlab);
   VC_CUDA(cudaMemcpyAsync(h.eps_d.p, eps_r, sizeof(double) * h.nlab, cudaMemcpyHostToDevice, h.stream));
+  h.gm.reset();                   // the restart-cycle graph points into the rebuilt tables
   VC_TRY(build_panels(h));
   VC_TRY(build_precond(h));
   h.have_rho = false;

@@ -155,6 +155,26 @@ struct Precond {
   DBuf<float> dscale_f;
 };
 
+// The instantiated graph of one GMRES restart cycle (a device-side while
+// loop over Arnoldi steps), kept per handle and rebuilt when its key (shape,
+// precision, workspace addresses, product variant) changes.
+struct GmresGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  uintptr_t key[10] = {0};
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+    for (auto& k : key) k = 0;
+  }
+  ~GmresGraph() { reset(); }
+  GmresGraph() = default;
+  GmresGraph(const GmresGraph&) = delete;
+  GmresGraph& operator=(const GmresGraph&) = delete;
+};
+
 struct Handle {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -211,6 +231,7 @@ struct Handle {
   DBuf<double> rhs;               // last capacitance RHS
   bool have_rho = false;
   DBuf<char> solver_ws;
+  GmresGraph gm;                  // restart-cycle graph (declared after the buffers it points into)
   double setup_s[6] = {0, 0, 0, 0, 0, 0};   // wall seconds of the set-up phases (voxcap_setup_times)
   HostMap act_map;                // GMRES: [2][nrhs] active flags per step parity, then the
                                   // cycle-end read-back of iteration counts and flags [2][nrhs]

@@ -257,11 +257,18 @@ __device__ __forceinline__ bool last_cta(unsigned* ticket, unsigned count) {
   return is_last;
 }
 
+// Control words of a restart cycle in device memory, written before each
+// launch of the cycle graph (so the graph itself never changes).
+struct CycleCtl {
+  double rtol;        // inner relative tolerance
+  int max_it;         // iteration cap of the solve
+  int steps;          // Arnoldi steps taken in this cycle (the loop guard)
+};
+
 struct StepArgs {
   int64_t N;
   int nrhs, m, nchunks, part_ld;
-  double rtol;
-  int max_it;
+  CycleCtl* ctl;
   int* jdev;
   double* partial;
   unsigned* tickets;     // [nrhs] per-column tickets
@@ -314,7 +321,7 @@ __global__ void k_gs_step(const T* __restrict__ V, T* __restrict__ w, int pass, 
     const double t = block_sum(acc, sh);
     if (threadIdx.x == 0) out[i] = t;
   }
-  if (pass == 2 && threadIdx.x == 0 && j < a.m) givens_col(s, col, a.m, j, a.rtol, a.max_it, a.invn);
+  if (pass == 2 && threadIdx.x == 0 && j < a.m) givens_col(s, col, a.m, j, a.ctl->rtol, a.ctl->max_it, a.invn);
 }
 
 // V[j+1] = w * invn and vcur = V[j+1] for the columns that took step j; the
@@ -340,12 +347,33 @@ __global__ void k_store_next(const T* __restrict__ w, T* __restrict__ V, T* __re
   if (last_cta(ticket, gridDim.x) && threadIdx.x == 0) *jdev = j + 1;
 }
 
+__global__ void k_cycle_ctl(CycleCtl* ctl, double rtol, int max_it) {
+  ctl->rtol = rtol;
+  ctl->max_it = max_it;
+  ctl->steps = 0;
+}
+
+// End of an Arnoldi step inside the cycle graph: run another step while some
+// column is active, the cycle has steps left (*jdev < m) and the loop guard
+// (steps counted here, independent of *jdev) has not reached m.
+__global__ void k_loop_cond(cudaGraphConditionalHandle hc, CycleCtl* ctl, const int* __restrict__ jdev,
+                            const int* __restrict__ active, int nrhs, int m) {
+  if (threadIdx.x != 0) return;
+  const int steps = ++ctl->steps;
+  int any = 0;
+  for (int c = 0; c < nrhs; ++c) any |= active[c];
+  cudaGraphSetConditional(hc, (any && *jdev < m && steps < m) ? 1u : 0u);
+}
+
 // Solve R A d = R r (x0 = 0) per column to a preconditioned relative
 // residual rtol.  r, d: device [nrhs][N] in T.  `adjoint`: use A^T.
-// One Arnoldi step (product, preconditioner, two Gram-Schmidt passes,
-// Givens update, next basis vector) is captured once as a CUDA graph whose
-// kernels read the step index from device memory; the host launches it
-// speculatively one step ahead of the convergence flags it reads back.
+// A restart cycle is one launch of a CUDA graph: the host prepares the
+// cycle's first basis vector, writes the cycle's control words, and launches
+// the graph, whose conditional while node runs Arnoldi steps (product,
+// preconditioner, two Gram-Schmidt passes with the Givens update, next basis
+// vector, loop condition) on the device until every column has converged or
+// the cycle is full; the host synchronises once per cycle, after the update
+// of d.  The graph is instantiated once per handle, shape and precision.
 template <typename T>
 static int gmres(Handle& h, const T* r, T* d, int nrhs, double rtol, int max_it, bool adjoint,
                  SolveCounters* cnt) {
@@ -358,7 +386,8 @@ static int gmres(Handle& h, const T* r, T* d, int nrhs, double rtol, int max_it,
   size_t bytes = sizeof(T) * (nV + 3 * nW) + 256;
   const size_t nd_H = (size_t)nrhs * (m + 1) * m, nd_cs = (size_t)nrhs * m, nd_g = (size_t)nrhs * (m + 1);
   const size_t ndbl = nd_H + 2 * nd_cs + 3 * nd_g + 3 * (size_t)nrhs + (size_t)nrhs * (m + 1) * nch;
-  bytes += sizeof(double) * ndbl + sizeof(int) * (3 * nrhs + 4) + sizeof(unsigned) * (nrhs + 1) + 256;
+  bytes += sizeof(double) * ndbl + sizeof(int) * (3 * nrhs + 4) + sizeof(unsigned) * (nrhs + 1) + 256 +
+           sizeof(CycleCtl) + 64;
   VC_TRY(h.solver_ws.alloc(bytes));
   char* wp = h.solver_ws.p;
   T* V = reinterpret_cast<T*>(wp); wp += sizeof(T) * nV;
@@ -384,6 +413,7 @@ static int gmres(Handle& h, const T* r, T* d, int nrhs, double rtol, int max_it,
   s.iters = ip; ip += nrhs;
   int* jdev = ip; ip += 1;
   unsigned* tickets = reinterpret_cast<unsigned*>(ip + 1);    // [nrhs] columns, [nrhs] the store
+  CycleCtl* ctl = reinterpret_cast<CycleCtl*>(((uintptr_t)(tickets + nrhs + 1) + 15) & ~(uintptr_t)15);
   VC_CUDA(cudaMemsetAsync(d, 0, sizeof(T) * nW, st));
   VC_CUDA(cudaMemsetAsync(tickets, 0, sizeof(unsigned) * (nrhs + 1), st));
   VC_TRY(h.act_map.ensure((size_t)4 * nrhs));
@@ -393,60 +423,81 @@ static int gmres(Handle& h, const T* r, T* d, int nrhs, double rtol, int max_it,
   // the product's tables and workspace must exist before capture (no
   // allocation or symbol copy inside the graph)
   VC_TRY(mvm_prepare(h, nrhs, sizeof(C_t<T>)));
-  const int64_t launches_before_capture = launch_count();
 
-  // ---- capture one Arnoldi step ----
-  cudaStream_t cap = nullptr;
-  VC_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  {
-    const cudaStream_t saved = h.stream;
-    h.stream = cap;
-    int rc = VOXCAP_OK;
-    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed) != cudaSuccess) rc = VOXCAP_ERR_CUDA;
-    if (rc == VOXCAP_OK) rc = mvm<T>(h, vcur, W, nrhs, adjoint, nullptr);
-    if (rc == VOXCAP_OK) rc = precond_apply<T>(h, W, W2, nrhs);
+  // ---- the restart-cycle graph, built once per key ----
+  const uintptr_t key[10] = {sizeof(T), (uintptr_t)adjoint, (uintptr_t)nrhs, (uintptr_t)N, (uintptr_t)m,
+                             (uintptr_t)h.solver_ws.p, (uintptr_t)h.ws.p,
+                             (uintptr_t)(h.path + 2) | ((uintptr_t)h.yvar << 8) | ((uintptr_t)h.zvar << 16) |
+                                 ((uintptr_t)(h.ztx + 2) << 24),
+                             (uintptr_t)(h.ytx[0] + 2) | ((uintptr_t)(h.ytx[1] + 2) << 8), (uintptr_t)h.act_map.d};
+  bool same = h.gm.exec != nullptr;
+  for (int i = 0; same && i < 10; ++i) same = h.gm.key[i] == key[i];
+  if (!same) {
+    h.gm.reset();
+    const int64_t launches_before_capture = launch_count();
+    cudaGraph_t graph = nullptr;
+    int rc = cudaGraphCreate(&graph, 0) == cudaSuccess ? VOXCAP_OK : VOXCAP_ERR_CUDA;
+    cudaGraphConditionalHandle hc = 0;
+    cudaGraph_t body = nullptr;
+    if (rc == VOXCAP_OK &&
+        cudaGraphConditionalHandleCreate(&hc, graph, 1, cudaGraphCondAssignDefault) != cudaSuccess)
+      rc = VOXCAP_ERR_CUDA;
     if (rc == VOXCAP_OK) {
-      dim3 gsw(nch, nrhs);
-      StepArgs sa;
-      sa.N = N; sa.nrhs = nrhs; sa.m = m; sa.nchunks = nch; sa.part_ld = m + 1;
-      sa.rtol = rtol; sa.max_it = max_it; sa.jdev = jdev; sa.partial = partial;
-      sa.tickets = tickets; sa.invn = invn;
-      k_gs_step<T><<<gsw, kDotTB, 0, cap>>>(V, W2, 0, s, sa);
-      k_gs_step<T><<<gsw, kDotTB, 0, cap>>>(V, W2, 1, s, sa);
-      k_gs_step<T><<<gsw, kDotTB, 0, cap>>>(V, W2, 2, s, sa);
-      k_store_next<T><<<gN, TB, 0, cap>>>(W2, V, vcur, s, sa, tickets + nrhs, h.act_map.d);
+      cudaGraphNodeParams np = {};
+      np.type = cudaGraphNodeTypeConditional;
+      np.conditional.handle = hc;
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      cudaGraphNode_t wn;
+      if (cudaGraphAddNode(&wn, graph, nullptr, nullptr, 0, &np) != cudaSuccess) rc = VOXCAP_ERR_CUDA;
+      else body = np.conditional.phGraph_out[0];
     }
-    cudaError_t ce = cudaStreamEndCapture(cap, &graph);
-    h.stream = saved;
-    if (rc == VOXCAP_OK && ce != cudaSuccess) rc = VOXCAP_ERR_CUDA;
+    cudaStream_t cap = nullptr;
+    if (rc == VOXCAP_OK && cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess)
+      rc = VOXCAP_ERR_CUDA;
+    if (rc == VOXCAP_OK) {
+      const cudaStream_t saved = h.stream;
+      h.stream = cap;
+      if (cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) !=
+          cudaSuccess)
+        rc = VOXCAP_ERR_CUDA;
+      if (rc == VOXCAP_OK) rc = mvm<T>(h, vcur, W, nrhs, adjoint, nullptr);
+      if (rc == VOXCAP_OK) rc = precond_apply<T>(h, W, W2, nrhs);
+      if (rc == VOXCAP_OK) {
+        dim3 gsw(nch, nrhs);
+        StepArgs sa;
+        sa.N = N; sa.nrhs = nrhs; sa.m = m; sa.nchunks = nch; sa.part_ld = m + 1;
+        sa.ctl = ctl; sa.jdev = jdev; sa.partial = partial;
+        sa.tickets = tickets; sa.invn = invn;
+        k_gs_step<T><<<gsw, kDotTB, 0, cap>>>(V, W2, 0, s, sa);
+        k_gs_step<T><<<gsw, kDotTB, 0, cap>>>(V, W2, 1, s, sa);
+        k_gs_step<T><<<gsw, kDotTB, 0, cap>>>(V, W2, 2, s, sa);
+        k_store_next<T><<<gN, TB, 0, cap>>>(W2, V, vcur, s, sa, tickets + nrhs, h.act_map.d);
+        k_loop_cond<<<1, 32, 0, cap>>>(hc, ctl, jdev, s.active, nrhs, m);
+      }
+      cudaGraph_t captured = nullptr;
+      const cudaError_t ce = cudaStreamEndCapture(cap, &captured);
+      h.stream = saved;
+      if (rc == VOXCAP_OK && ce != cudaSuccess) rc = VOXCAP_ERR_CUDA;
+    }
+    if (cap) cudaStreamDestroy(cap);
+    cudaGraphExec_t exec = nullptr;
     if (rc == VOXCAP_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) rc = VOXCAP_ERR_CUDA;
-    if (graph) cudaGraphDestroy(graph);
-    cudaStreamDestroy(cap);
     adjust_launch_count(launches_before_capture - launch_count());   // capture issued no launch
     if (rc != VOXCAP_OK) {
       if (exec) cudaGraphExecDestroy(exec);
-      (void)cudaGetLastError();
-      set_error("capture of the GMRES step failed");
-      return rc;
+      if (graph) cudaGraphDestroy(graph);
+      const cudaError_t e = cudaGetLastError();
+      set_error(std::string("building the GMRES cycle graph failed: ") + cudaGetErrorString(e));
+      return VOXCAP_ERR_CUDA;
     }
+    h.gm.graph = graph;
+    h.gm.exec = exec;
+    for (int i = 0; i < 10; ++i) h.gm.key[i] = key[i];
   }
-  struct ExecGuard {
-    cudaGraphExec_t e;
-    ~ExecGuard() { if (e) cudaGraphExecDestroy(e); }
-  } guard{exec};
-  // kernel launches inside one step (counted per replay)
+  // kernel launches inside one Arnoldi step of the graph (counted per step run)
   const int step_launches = 5 + ((h.pre.kind == VOXCAP_PRECOND_BDD || h.pre.kind == VOXCAP_PRECOND_BD) &&
-                                 h.pre.nblocks > 0 && h.pre.max_n > 0 ? 2 : 1) + 4;
-
-  cudaEvent_t ev[2];
-  VC_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
-  VC_CUDA(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
-  struct EvGuard {
-    cudaEvent_t* e;
-    ~EvGuard() { cudaEventDestroy(e[0]); cudaEventDestroy(e[1]); }
-  } eguard{ev};
+                                 h.pre.nblocks > 0 && h.pre.max_n > 0 ? 2 : 1) + 5;
 
   bool first = true;
   int total_it = 0;
@@ -467,42 +518,29 @@ static int gmres(Handle& h, const T* r, T* d, int nrhs, double rtol, int max_it,
     k_scale_cols<T><<<gN, TB, 0, st>>>(V, N, nrhs, invn, nullptr); ::vc::note_launch();
     VC_CUDA(cudaMemcpyAsync(vcur, V, sizeof(T) * nW, cudaMemcpyDeviceToDevice, st));
     VC_CUDA(cudaMemsetAsync(jdev, 0, sizeof(int), st));
+    k_cycle_ctl<<<1, 1, 0, st>>>(ctl, rtol, max_it); ::vc::note_launch();
     VC_CUDA(cudaGetLastError());
     first = false;
-    // Arnoldi steps: launch step j+1 before reading the flags of step j
-    int launched = 0, checked = 0;
-    bool done = false;
-    auto launch_step = [&]() -> int {
-      VC_CUDA(cudaGraphLaunch(exec, st));
-      for (int q = 0; q < step_launches; ++q) ::vc::note_launch();
-      cnt->matvecs += 1;
-      VC_CUDA(cudaEventRecord(ev[launched & 1], st));
-      ++launched;
-      return VOXCAP_OK;
-    };
-    VC_TRY(launch_step());
-    while (!done) {
-      if (launched < m) VC_TRY(launch_step());
-      VC_CUDA(cudaEventSynchronize(ev[checked & 1]));
-      const volatile int* a = h.act_map.h + (checked & 1) * nrhs;   // written by step `checked`
-      ++checked;
-      bool any = false;
-      for (int c = 0; c < nrhs; ++c) any = any || a[c];
-      if (!any || checked >= m) done = true;
-    }
-    total_it += checked;
+    // the Arnoldi steps of the cycle run on the device
+    VC_CUDA(cudaGraphLaunch(h.gm.exec, st));
     k_backsolve<<<gC, 64, 0, st>>>(s, nrhs, m); ::vc::note_launch();
     k_update_x<T><<<gN, TB, 0, st>>>(d, V, N, nrhs, s.hcol, s.kused, m); ::vc::note_launch();
     // a column that stopped only because the cycle ended is still unconverged:
     // re-activate it from the residual estimate (converged ones stay inactive)
     k_reactivate<<<gC, 64, 0, st>>>(s, nrhs, m, rtol, max_it); ::vc::note_launch();
     VC_CUDA(cudaGetLastError());
-    // iteration counts and active flags in one read-back (mapped pinned host memory)
+    // steps taken, iteration counts and active flags in one read-back
+    // (mapped pinned host memory): the one synchronisation of the cycle
     int* its_h = h.act_map.h + 2 * nrhs;
     int* act_h = h.act_map.h + 3 * nrhs;
+    int steps_h = 0;
     VC_CUDA(cudaMemcpyAsync(its_h, s.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
     VC_CUDA(cudaMemcpyAsync(act_h, s.active, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
+    VC_CUDA(cudaMemcpyAsync(&steps_h, &ctl->steps, sizeof(int), cudaMemcpyDeviceToHost, st));
     VC_CUDA(cudaStreamSynchronize(st));
+    for (int q = 0; q < steps_h * step_launches; ++q) ::vc::note_launch();
+    cnt->matvecs += steps_h;
+    total_it += steps_h;
     int maxit = 0;
     bool any = false;
     for (int c = 0; c < nrhs; ++c) {

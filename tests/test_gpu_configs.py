@@ -185,3 +185,24 @@ def test_meanders_large():
     C64, _ = v64.capacitance(tol=1e-8)
     assert np.max(np.abs(C32 - C64)) <= 1e-4 * np.max(np.abs(C64))
     _cap_properties(C64)
+
+
+def test_meanders_tucker_restored_matches_generated():
+    """512 x 512 x 64 meanders with the Toeplitz tensors restored from Tucker
+    factors at tolerance 1e-6 (installed on a 514^3 index cube, Eq. 13) on the
+    tensor cores, against tensors generated directly: every C entry within
+    1e-4 of the largest."""
+    import torch
+    from paper_2004_02609_gb300 import tucker as T
+    from paper_2004_02609_gb300 import voxcap as V
+    w = W.meanders()
+    lab = torch.tensor(w.labels, device="cuda")
+    model = T.install(max(w.labels.shape) + 2, 1e-6)
+    vt = V.VoxCap(lab, w.conductor_id, w.eps_r, w.voxel_size, tucker=model)
+    Ct, st = vt.capacitance(tol=1e-6)
+    assert st["converged"] == 1
+    vt.close()
+    vg = V.VoxCap(lab, w.conductor_id, w.eps_r, w.voxel_size)
+    Cg, _ = vg.capacitance(tol=1e-6)
+    assert np.max(np.abs(Ct - Cg)) <= 1e-4 * np.max(np.abs(Cg))
+    _cap_properties(Ct)
