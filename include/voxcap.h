@@ -268,6 +268,24 @@ int voxcap_capacitance(voxcap_t* h, double tol, double* C_host, double* rho_dev,
                        voxcap_stats* st);
 
 /*
+ * voxcap_capacitance_columns -- columns j0 .. j1-1 of the capacitance
+ * matrices (Eq. 8): the unit-potential solves of conductors j0 .. j1-1 only,
+ * in one batch.  A column's solve does not depend on which other columns
+ * share its batch (every reduction is summed in an order fixed by N, every
+ * column keeps its own tolerances), so column blocks computed apart -- on
+ * several GPUs, each with its own handle of the same structure -- assemble
+ * into the matrix voxcap_capacitance returns, bit for bit (the multi-GPU
+ * sharding of conductors).
+ *  C_host  host double: for each structure the m x (j1-j0) row-major block
+ *          (rows = all conductors i, columns = conductors j0 .. j1-1), back
+ *          to back.
+ * Returns VOXCAP_ERR_ARG for a range outside [0, m) and the codes of
+ * voxcap_capacitance.  Does not enable voxcap_capacitance_grad unless the
+ * range covers every conductor.
+ */
+int voxcap_capacitance_columns(voxcap_t* h, double tol, int j0, int j1, double* C_host, voxcap_stats* st);
+
+/*
  * voxcap_capacitance_grad -- dL/d eps_r[label] for L = sum_s sum_ij
  * dL_dC[s][i][j] C_s,ij, by one batched adjoint solve A^T mu = W dL_dC that
  * reuses the FFT'd kernels (conjugated), the forward charges of the last
@@ -360,7 +378,8 @@ int64_t voxcap_launch_count(void);
  * inverse y passes' columns per CTA, 0..4, or -1 for the default width.
  * z_order = -1 re-runs the set-up autotuner, which times the variants on
  * this handle's own products and keeps the fastest (its choice is cached per
- * device, grid and batch); the other arguments are then ignored.
+ * device, grid and batch); z_order = -2 changes nothing (query); the other
+ * arguments are then ignored.
  * choice_out (may be NULL) receives {z_order, z_tile_log2, y_fwd_log2,
  * y_inv_log2} in force.  Forcing a variant (z_order >= 0) selects the
  * generic passes (product path 0, see voxcap_set_product_path).  Returns

@@ -235,6 +235,16 @@ int voxcap_capacitance(voxcap_t* hv, double tol, double* C_host, double* rho_dev
   return capacitance(hv->h, tol, C_host, rho_dev, st);
 }
 
+int voxcap_capacitance_columns(voxcap_t* hv, double tol, int j0, int j1, double* C_host, voxcap_stats* st) {
+  VC_CHECK(hv != nullptr, VOXCAP_ERR_ARG, "NULL handle");
+  set_alloc_stream(hv->h.stream);
+  VC_CHECK(C_host != nullptr, VOXCAP_ERR_ARG, "C_host is NULL");
+  VC_CHECK(tol > 0.0 && tol < 1.0, VOXCAP_ERR_ARG, "tol must be in (0, 1)");
+  VC_CHECK(hv->h.pan.m_max > 0, VOXCAP_ERR_NO_CONDUCTOR, "no conductor in the material table");
+  VC_CHECK(j0 >= 0 && j1 > j0 && j1 <= hv->h.pan.m_max, VOXCAP_ERR_ARG, "conductor range outside [0, m)");
+  return capacitance_cols(hv->h, tol, j0, j1, C_host, nullptr, st);
+}
+
 int voxcap_capacitance_grad(voxcap_t* hv, const double* dL_dC_host, double tol, double* grad_host,
                             voxcap_stats* st) {
   VC_CHECK(hv != nullptr, VOXCAP_ERR_ARG, "NULL handle");
@@ -280,13 +290,15 @@ int voxcap_set_product_tiles(voxcap_t* hv, int z_order, int z_tile_log2, int y_f
                              int* choice_out) {
   VC_CHECK(hv != nullptr, VOXCAP_ERR_ARG, "NULL handle");
   Handle& h = hv->h;
-  VC_CHECK(z_order >= -1 && z_order <= 1, VOXCAP_ERR_ARG, "z_order must be -1, 0 or 1");
+  VC_CHECK(z_order >= -2 && z_order <= 1, VOXCAP_ERR_ARG, "z_order must be -2, -1, 0 or 1");
   if (z_order >= 0)
     VC_CHECK(z_tile_log2 >= 0 && z_tile_log2 <= 4 && y_fwd_log2 >= -1 && y_fwd_log2 <= 4 &&
                  y_inv_log2 >= -1 && y_inv_log2 <= 4,
              VOXCAP_ERR_ARG, "tile widths out of range");
   set_alloc_stream(h.stream);
-  if (z_order < 0) {
+  if (z_order == -2) {
+    // query only
+  } else if (z_order < 0) {
     VC_TRY(retune_products(h));
   } else {
     h.path = 0;                       // a forced variant is one of the generic passes

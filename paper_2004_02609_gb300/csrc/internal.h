@@ -290,6 +290,7 @@ int precond_apply(Handle& h, const T* r, T* z, int nrhs);
 int solve(Handle& h, const double* B, int nrhs, double tol, double* X, voxcap_stats* st,
           bool adjoint);
 int capacitance(Handle& h, double tol, double* C_host, double* rho_dev, voxcap_stats* st);
+int capacitance_cols(Handle& h, double tol, int j0, int j1, double* C_host, double* rho_dev, voxcap_stats* st);
 int capacitance_grad(Handle& h, const double* dLdC, double tol, double* grad_host,
                      voxcap_stats* st);
 // entries evaluated on arbitrary (kind, orientations, centre difference)

@@ -134,12 +134,12 @@ __global__ void k_cycle_start(GState s, int nrhs, int m, bool first, double* inv
 
 // after a cycle: a column is unconverged if its residual estimate is above
 // rtol * beta0 and it has iterations left; mark it active for the next cycle
-__global__ void k_reactivate(GState s, int nrhs, int m, double rtol, int max_it) {
+__global__ void k_reactivate(GState s, int nrhs, int m, const double* __restrict__ rtol, int max_it) {
   const int col = blockIdx.x * blockDim.x + threadIdx.x;
   if (col >= nrhs) return;
   const int k = s.kused[col];
   const double res = fabs(s.g[(int64_t)col * (m + 1) + k]);
-  s.active[col] = (s.beta0[col] > 0.0 && res > rtol * s.beta0[col] && s.iters[col] < max_it) ? 1 : 0;
+  s.active[col] = (s.beta0[col] > 0.0 && res > rtol[col] * s.beta0[col] && s.iters[col] < max_it) ? 1 : 0;
 }
 
 // y = H^-1 g (upper triangular, k x k), stored in hcol
@@ -199,11 +199,14 @@ struct SolveCounters {
 };
 
 // chunks per column of the dot/update sweeps: at least one per 1024 rows,
-// and for small systems enough (down to 128 rows each) to cover about 304
-// CTAs over all columns -- the FP64 inner products run at a low per-SM rate
-static int nchunks_for(int64_t N, int nrhs) {
+// and for small systems enough (down to 128 rows each) for about one CTA per
+// SM per column -- the FP64 inner products run at a low per-SM rate
+// The count depends on N only, so a column's reductions are summed in the
+// same order whatever other columns share its batch (a column's solve is
+// bit-for-bit the same alone or batched; the sharded capacitance relies on it).
+static int nchunks_for(int64_t N, int /*nrhs*/) {
   int64_t c = (N + 1023) / 1024;
-  const int64_t fine = std::min<int64_t>((N + 127) / 128, (304 + nrhs - 1) / std::max(nrhs, 1));
+  const int64_t fine = std::min<int64_t>((N + 127) / 128, 152);
   c = std::max(c, fine);
   if (c < 1) c = 1;
   if (c > 2048) c = 2048;
@@ -260,7 +263,6 @@ __device__ __forceinline__ bool last_cta(unsigned* ticket, unsigned count) {
 // Control words of a restart cycle in device memory, written before each
 // launch of the cycle graph (so the graph itself never changes).
 struct CycleCtl {
-  double rtol;        // inner relative tolerance
   int max_it;         // iteration cap of the solve
   int steps;          // Arnoldi steps taken in this cycle (the loop guard)
 };
@@ -269,6 +271,7 @@ struct StepArgs {
   int64_t N;
   int nrhs, m, nchunks, part_ld;
   CycleCtl* ctl;
+  const double* rtol;   // [nrhs] inner relative tolerance of each column
   int* jdev;
   double* partial;
   unsigned* tickets;     // [nrhs] per-column tickets
@@ -321,7 +324,7 @@ __global__ void k_gs_step(const T* __restrict__ V, T* __restrict__ w, int pass, 
     const double t = block_sum(acc, sh);
     if (threadIdx.x == 0) out[i] = t;
   }
-  if (pass == 2 && threadIdx.x == 0 && j < a.m) givens_col(s, col, a.m, j, a.ctl->rtol, a.ctl->max_it, a.invn);
+  if (pass == 2 && threadIdx.x == 0 && j < a.m) givens_col(s, col, a.m, j, a.rtol[col], a.ctl->max_it, a.invn);
 }
 
 // V[j+1] = w * invn and vcur = V[j+1] for the columns that took step j; the
@@ -347,8 +350,7 @@ __global__ void k_store_next(const T* __restrict__ w, T* __restrict__ V, T* __re
   if (last_cta(ticket, gridDim.x) && threadIdx.x == 0) *jdev = j + 1;
 }
 
-__global__ void k_cycle_ctl(CycleCtl* ctl, double rtol, int max_it) {
-  ctl->rtol = rtol;
+__global__ void k_cycle_ctl(CycleCtl* ctl, int max_it) {
   ctl->max_it = max_it;
   ctl->steps = 0;
 }
@@ -366,8 +368,8 @@ __global__ void k_loop_cond(cudaGraphConditionalHandle hc, CycleCtl* ctl, const 
 }
 
 // Solve R A d = R r (x0 = 0) per column to a preconditioned relative
-// residual rtol.  r, d: device [nrhs][N] in T.  `adjoint`: use A^T.
-// A restart cycle is one launch of a CUDA graph: the host prepares the
+// residual rtol_host[col] (host, one per column).  r, d: device [nrhs][N] in T.
+// `adjoint`: use A^T.  A restart cycle is one launch of a CUDA graph: the host prepares the
 // cycle's first basis vector, writes the cycle's control words, and launches
 // the graph, whose conditional while node runs Arnoldi steps (product,
 // preconditioner, two Gram-Schmidt passes with the Givens update, next basis
@@ -375,7 +377,7 @@ __global__ void k_loop_cond(cudaGraphConditionalHandle hc, CycleCtl* ctl, const 
 // the cycle is full; the host synchronises once per cycle, after the update
 // of d.  The graph is instantiated once per handle, shape and precision.
 template <typename T>
-static int gmres(Handle& h, const T* r, T* d, int nrhs, double rtol, int max_it, bool adjoint,
+static int gmres(Handle& h, const T* r, T* d, int nrhs, const double* rtol_host, int max_it, bool adjoint,
                  SolveCounters* cnt) {
   const int64_t N = h.pan.N;
   const int m = std::max(1, h.opts.restart);
@@ -387,7 +389,7 @@ static int gmres(Handle& h, const T* r, T* d, int nrhs, double rtol, int max_it,
   const size_t nd_H = (size_t)nrhs * (m + 1) * m, nd_cs = (size_t)nrhs * m, nd_g = (size_t)nrhs * (m + 1);
   const size_t ndbl = nd_H + 2 * nd_cs + 3 * nd_g + 3 * (size_t)nrhs + (size_t)nrhs * (m + 1) * nch;
   bytes += sizeof(double) * ndbl + sizeof(int) * (3 * nrhs + 4) + sizeof(unsigned) * (nrhs + 1) + 256 +
-           sizeof(CycleCtl) + 64;
+           sizeof(CycleCtl) + sizeof(double) * nrhs + 64;
   VC_TRY(h.solver_ws.alloc(bytes));
   char* wp = h.solver_ws.p;
   T* V = reinterpret_cast<T*>(wp); wp += sizeof(T) * nV;
@@ -414,6 +416,8 @@ static int gmres(Handle& h, const T* r, T* d, int nrhs, double rtol, int max_it,
   int* jdev = ip; ip += 1;
   unsigned* tickets = reinterpret_cast<unsigned*>(ip + 1);    // [nrhs] columns, [nrhs] the store
   CycleCtl* ctl = reinterpret_cast<CycleCtl*>(((uintptr_t)(tickets + nrhs + 1) + 15) & ~(uintptr_t)15);
+  double* rtol = reinterpret_cast<double*>(((uintptr_t)(ctl + 1) + 15) & ~(uintptr_t)15);
+  VC_CUDA(cudaMemcpyAsync(rtol, rtol_host, sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
   VC_CUDA(cudaMemsetAsync(d, 0, sizeof(T) * nW, st));
   VC_CUDA(cudaMemsetAsync(tickets, 0, sizeof(unsigned) * (nrhs + 1), st));
   VC_TRY(h.act_map.ensure((size_t)4 * nrhs));
@@ -467,7 +471,7 @@ static int gmres(Handle& h, const T* r, T* d, int nrhs, double rtol, int max_it,
         dim3 gsw(nch, nrhs);
         StepArgs sa;
         sa.N = N; sa.nrhs = nrhs; sa.m = m; sa.nchunks = nch; sa.part_ld = m + 1;
-        sa.ctl = ctl; sa.jdev = jdev; sa.partial = partial;
+        sa.ctl = ctl; sa.rtol = rtol; sa.jdev = jdev; sa.partial = partial;
         sa.tickets = tickets; sa.invn = invn;
         k_gs_step<T><<<gsw, kDotTB, 0, cap>>>(V, W2, 0, s, sa);
         k_gs_step<T><<<gsw, kDotTB, 0, cap>>>(V, W2, 1, s, sa);
@@ -518,7 +522,7 @@ static int gmres(Handle& h, const T* r, T* d, int nrhs, double rtol, int max_it,
     k_scale_cols<T><<<gN, TB, 0, st>>>(V, N, nrhs, invn, nullptr); ::vc::note_launch();
     VC_CUDA(cudaMemcpyAsync(vcur, V, sizeof(T) * nW, cudaMemcpyDeviceToDevice, st));
     VC_CUDA(cudaMemsetAsync(jdev, 0, sizeof(int), st));
-    k_cycle_ctl<<<1, 1, 0, st>>>(ctl, rtol, max_it); ::vc::note_launch();
+    k_cycle_ctl<<<1, 1, 0, st>>>(ctl, max_it); ::vc::note_launch();
     VC_CUDA(cudaGetLastError());
     first = false;
     // the Arnoldi steps of the cycle run on the device
@@ -613,8 +617,7 @@ int solve(Handle& h, const double* B, int nrhs, double tol, double* X, voxcap_st
     if (sw == 0) rn = bn;                            // the first residual is B itself
     else VC_TRY(col_norms(h, R64.p, nrhs, rn, dpart.p, dnorm.p));
     worst = 0.0;
-    std::vector<double> f(nrhs), finv(nrhs);
-    double need = 0.0;   // largest reduction still needed
+    std::vector<double> f(nrhs), finv(nrhs), itol(nrhs);
     for (int c = 0; c < nrhs; ++c) {
       double rel = bn[c] > 0.0 ? rn[c] / bn[c] : 0.0;
       worst = std::max(worst, rel);
@@ -622,34 +625,30 @@ int solve(Handle& h, const double* B, int nrhs, double tol, double* X, voxcap_st
       bool done = rel <= tol || rn[c] == 0.0;
       f[c] = done ? 0.0 : 1.0 / rn[c];
       finv[c] = done ? 0.0 : rn[c];
-      if (!done) need = std::max(need, tol / rel);
+      // inner tolerance of the column (its own, so that a column's solve does
+      // not depend on the others in the batch).  Plain FP64: aim to finish in
+      // this sweep.  FP32 inside refinement: a sweep reduces the residual by
+      // inner_tol at most (FP32 GMRES stagnates when pushed much further,
+      // and its Krylov space is rebuilt each sweep anyway) and by no more
+      // than finishing needs, so the last sweep does not over-solve
+      const double need = done ? 1.0 : tol / rel;
+      itol[c] = refine ? std::max(5e-6, std::max(h.opts.inner_tol, 0.5 * need))
+                       : std::min(1e-2, std::max(1e-14, 0.5 * need));
     }
     if (worst <= tol) { conv = true; break; }
     if (sw == max_sweeps || cnt.iters >= h.opts.max_iters) break;
     ++sweeps;
-    // inner tolerance.  Plain FP64: aim to finish in this sweep.  FP32 inside
-    // refinement: a sweep reduces its residual by inner_tol at most (FP32
-    // GMRES stagnates when pushed much further, and its Krylov space is
-    // rebuilt each sweep anyway) and by no more than finishing needs, so the
-    // last sweep does not over-solve
-    double itol;
-    if (refine) {
-      const double floor_t = 5e-6;
-      itol = std::max(floor_t, std::max(h.opts.inner_tol, 0.5 * need));
-    } else {
-      itol = std::min(1e-2, std::max(1e-14, 0.5 * need));
-    }
     int left = std::max(1, h.opts.max_iters - cnt.iters);
     VC_CUDA(cudaMemcpyAsync(fac.p, f.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
     if (refine) {
       k_cast_scaled<<<gN, TB, 0, s>>>(R64.p, rf.p, N, nrhs, fac.p); ::vc::note_launch();
-      VC_TRY(gmres<float>(h, rf.p, df.p, nrhs, itol, left, adjoint, &cnt));
+      VC_TRY(gmres<float>(h, rf.p, df.p, nrhs, itol.data(), left, adjoint, &cnt));
       VC_CUDA(cudaMemcpyAsync(fac.p, finv.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
       k_add_scaled<float><<<gN, TB, 0, s>>>(X, df.p, N, nrhs, fac.p); ::vc::note_launch();
     } else {
       // scale the FP64 residual to unit norm too (keeps the criterion relative)
       k_scale_cols<double><<<gN, TB, 0, s>>>(R64.p, N, nrhs, fac.p, nullptr); ::vc::note_launch();
-      VC_TRY(gmres<double>(h, R64.p, d64.p, nrhs, itol, left, adjoint, &cnt));
+      VC_TRY(gmres<double>(h, R64.p, d64.p, nrhs, itol.data(), left, adjoint, &cnt));
       VC_CUDA(cudaMemcpyAsync(fac.p, finv.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
       k_add_scaled<double><<<gN, TB, 0, s>>>(X, d64.p, N, nrhs, fac.p); ::vc::note_launch();
     }
@@ -672,60 +671,73 @@ int solve(Handle& h, const double* B, int nrhs, double tol, double* X, voxcap_st
 }
 
 // ------------------------------------------------------------------ capacitance
-__global__ void k_unit_rhs(int64_t N, int m, const int8_t* kind, const int16_t* owner, double* B) {
+// B[jj][p] = 1 on the conductor panels of conductor j0 + jj, else 0
+__global__ void k_unit_rhs(int64_t N, int j0, int nj, const int8_t* kind, const int16_t* owner, double* B) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= N * m) return;
-  const int j = (int)(t / N);
+  if (t >= N * nj) return;
+  const int j = j0 + (int)(t / N);
   const int64_t p = t % N;
   B[t] = (kind[p] == 0 && owner[p] == j) ? 1.0 : 0.0;
 }
 
-// C'[s][i][j] = sum_{p in structure s, conductor i} qscale_p rho_j[p]
-__global__ void k_cap_reduce(int64_t N, int m, const int64_t* off, const int64_t* ncond,
+// C'[s][i][jj] = sum_{p in structure s, conductor i} qscale_p rho_jj[p]
+__global__ void k_cap_reduce(int64_t N, int m, int nj, const int64_t* off, const int64_t* ncond,
                              const int16_t* owner, const double* qscale, const double* rho,
                              double* Cn) {
   __shared__ double sh[32];
-  const int s = blockIdx.x, i = blockIdx.y, j = blockIdx.z;
+  const int s = blockIdx.x, i = blockIdx.y, jj = blockIdx.z;
   const int64_t lo = off[s], hi = lo + ncond[s];
   double acc = 0.0;
   for (int64_t p = lo + threadIdx.x; p < hi; p += blockDim.x)
-    if (owner[p] == i) acc += qscale[p] * rho[(int64_t)j * N + p];
+    if (owner[p] == i) acc += qscale[p] * rho[(int64_t)jj * N + p];
   double v = block_sum(acc, sh);
-  if (threadIdx.x == 0) Cn[((int64_t)s * m + i) * m + j] = v;
+  if (threadIdx.x == 0) Cn[((int64_t)s * m + i) * nj + jj] = v;
 }
 
-int capacitance(Handle& h, double tol, double* C_host, double* rho_dev, voxcap_stats* st) {
+// Columns j0 .. j1-1 of the capacitance matrices (Eq. 8): one unit-potential
+// solve per conductor in the range, all in one batch, then the charge sums.
+// Every column is solved exactly as in the full batch (its solve does not
+// depend on the other columns), so column blocks computed apart -- e.g. on
+// different GPUs -- assemble into the same matrix bit for bit.
+int capacitance_cols(Handle& h, double tol, int j0, int j1, double* C_host, double* rho_dev, voxcap_stats* st) {
   const int m = h.pan.m_max;
   const int S = h.pan.S;
   const int64_t N = h.pan.N;
   VC_CHECK(m > 0, VOXCAP_ERR_NO_CONDUCTOR, "no conductor in the material table");
+  VC_CHECK(j0 >= 0 && j1 > j0 && j1 <= m, VOXCAP_ERR_ARG, "conductor range outside [0, m)");
+  const int nj = j1 - j0;
   VC_TRY(h.rhs.alloc((size_t)N * m));
   VC_TRY(h.rho.alloc((size_t)N * m));
   const int TB = 256;
-  k_unit_rhs<<<(unsigned)((N * m + TB - 1) / TB), TB, 0, h.stream>>>(N, m, h.pan.kind.p, h.pan.owner.p,
-                                                                      h.rhs.p); ::vc::note_launch();
+  k_unit_rhs<<<(unsigned)((N * nj + TB - 1) / TB), TB, 0, h.stream>>>(N, j0, nj, h.pan.kind.p, h.pan.owner.p,
+                                                                       h.rhs.p); ::vc::note_launch();
   VC_CUDA(cudaGetLastError());
-  int rc = solve(h, h.rhs.p, m, tol, h.rho.p, st, false);
+  int rc = solve(h, h.rhs.p, nj, tol, h.rho.p, st, false);
   if (rc != VOXCAP_OK && rc != VOXCAP_ERR_NOT_CONVERGED) return rc;
-  h.have_rho = true;
+  h.have_rho = (j0 == 0 && j1 == m);   // the adjoint gradient needs every column
   DBuf<int64_t> offd, ncd;
   DBuf<double> Cn;
   VC_TRY(offd.alloc(S));
   VC_TRY(ncd.alloc(S));
-  VC_TRY(Cn.alloc((size_t)S * m * m));
+  VC_TRY(Cn.alloc((size_t)S * m * nj));
   VC_CUDA(cudaMemcpyAsync(offd.p, h.pan.off.data(), sizeof(int64_t) * S, cudaMemcpyHostToDevice, h.stream));
   VC_CUDA(cudaMemcpyAsync(ncd.p, h.pan.nc.data(), sizeof(int64_t) * S, cudaMemcpyHostToDevice, h.stream));
-  k_cap_reduce<<<dim3(S, m, m), TB, 0, h.stream>>>(N, m, offd.p, ncd.p, h.pan.owner.p, h.pan.qscale.p,
-                                                  h.rho.p, Cn.p); ::vc::note_launch();
+  k_cap_reduce<<<dim3(S, m, nj), TB, 0, h.stream>>>(N, m, nj, offd.p, ncd.p, h.pan.owner.p, h.pan.qscale.p,
+                                                   h.rho.p, Cn.p); ::vc::note_launch();
   VC_CUDA(cudaGetLastError());
-  std::vector<double> cn((size_t)S * m * m);
+  std::vector<double> cn((size_t)S * m * nj);
   VC_CUDA(cudaMemcpyAsync(cn.data(), Cn.p, sizeof(double) * cn.size(), cudaMemcpyDeviceToHost, h.stream));
   VC_CUDA(cudaStreamSynchronize(h.stream));
   const double eps0 = 8.8541878128e-12;
   for (size_t q = 0; q < cn.size(); ++q) C_host[q] = eps0 * h.dv * cn[q];
   if (rho_dev)
-    VC_CUDA(cudaMemcpy(rho_dev, h.rho.p, sizeof(double) * (size_t)N * m, cudaMemcpyDeviceToDevice));
+    VC_CUDA(cudaMemcpy(rho_dev, h.rho.p, sizeof(double) * (size_t)N * nj, cudaMemcpyDeviceToDevice));
   return rc;
+}
+
+int capacitance(Handle& h, double tol, double* C_host, double* rho_dev, voxcap_stats* st) {
+  VC_CHECK(h.pan.m_max > 0, VOXCAP_ERR_NO_CONDUCTOR, "no conductor in the material table");
+  return capacitance_cols(h, tol, 0, h.pan.m_max, C_host, rho_dev, st);
 }
 
 }  // namespace vc

@@ -27,7 +27,7 @@ EPS0 = 8.8541878128e-12
 # exported symbols, in header order (checked by the CPU tests)
 SYMBOLS = ["voxcap_default_opts", "voxcap_last_error", "voxcap_setup", "voxcap_destroy",
            "voxcap_num_panels", "voxcap_panel_map", "voxcap_matvec", "voxcap_solve",
-           "voxcap_capacitance", "voxcap_capacitance_grad", "voxcap_update_eps",
+           "voxcap_capacitance", "voxcap_capacitance_columns", "voxcap_capacitance_grad", "voxcap_update_eps",
            "voxcap_entries", "voxcap_fft_length", "voxcap_toeplitz", "voxcap_launch_count",
            "voxcap_matvec_noalloc", "voxcap_tucker_expand", "voxcap_canonical_tensors",
            "voxcap_set_product_tiles", "voxcap_setup_times", "voxcap_set_product_path"]
@@ -86,6 +86,7 @@ def lib():
         L.voxcap_matvec.argtypes = [vp, vp, vp, i32, i32, i32]
         L.voxcap_solve.argtypes = [vp, vp, i32, dbl, vp, P(Stats)]
         L.voxcap_capacitance.argtypes = [vp, dbl, vp, vp, P(Stats)]
+        L.voxcap_capacitance_columns.argtypes = [vp, dbl, i32, i32, vp, P(Stats)]
         L.voxcap_capacitance_grad.argtypes = [vp, vp, dbl, vp, P(Stats)]
         L.voxcap_update_eps.argtypes = [vp, vp]
         L.voxcap_entries.argtypes = [i32, vp, vp, vp, vp, vp]
@@ -208,8 +209,9 @@ class VoxCap:
 
     def set_product_tiles(self, z_order=-1, z_tile_log2=4, y_fwd_log2=-1, y_inv_log2=-1):
         """Force the launch variant of the FP32 products (z radix order 0/1,
-        tile widths as log2; -1 = default y width), or re-run the autotuner
-        (z_order=-1); returns the choice in force as a 4-tuple."""
+        tile widths as log2; -1 = default y width), re-run the autotuner
+        (z_order=-1) or only query (z_order=-2); returns the choice in force
+        as a 4-tuple."""
         out = (ctypes.c_int * 4)()
         _check(lib().voxcap_set_product_tiles(self._h, z_order, z_tile_log2, y_fwd_log2, y_inv_log2, out))
         return tuple(out)
@@ -310,6 +312,18 @@ class VoxCap:
         if return_charges:
             return res, st.as_dict(), rho
         return res, st.as_dict()
+
+    def capacitance_columns(self, j0, j1, tol=1e-6, allow_unconverged=False):
+        """Columns j0..j1-1 of the capacitance matrix (farads, [m, j1-j0]) of
+        a single structure: the solves of those conductors only."""
+        m = self.structs[0]["n_conductors"]
+        C = np.zeros(self.n_struct * m * (j1 - j0), np.float64)
+        st = Stats()
+        rc = lib().voxcap_capacitance_columns(self._h, float(tol), int(j0), int(j1), C.ctypes.data,
+                                              ctypes.byref(st))
+        _check(rc, allow=(ERR_NOT_CONVERGED,) if allow_unconverged else ())
+        out = C.reshape(self.n_struct, m, j1 - j0)
+        return (out[0] if self.n_struct == 1 else list(out)), st.as_dict()
 
     def capacitance_grad(self, dL_dC, tol=1e-6):
         """dL/d eps_r[label] for L = sum(dL_dC * C), after capacitance()."""
