@@ -23,6 +23,7 @@ count.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   python bench.py --products --workload bus [--path 0|1]   (product timing only)
+  python bench.py --setup --workload pillars                (set-up timing only)
 
 Under torchrun (N > 1) every rank runs its own replica of the workload
 (independent extractions, no data-path collective): weak scaling.
@@ -565,6 +566,29 @@ def run_products(args):
             "frac_of_" + src + "_hbm": b / t / 1e9 / hbm, "sources": product_sources_hash()}
 
 
+def run_setup(args):
+    """Set-up only (--setup): the workload's set-up with its Toeplitz tensors
+    restored from Tucker factors (tolerance 1e-6, installed first) and with
+    them generated in FP64, K times each; prints the phase times (profiling
+    aid for the tensor-core restoration)."""
+    import torch
+    import __graft_entry__ as ge
+    from paper_2004_02609_gb300 import voxcap as V
+    ge.build()
+    w, desc = workload(args.workload)
+    lab = torch.tensor(w.labels, device="cuda")
+    model, t_install = install_tucker(max(w.labels.shape) + 2, TUCKER_TOL, 0, 1)
+    out = {"mode": "setup", "workload": desc, "install_s": t_install, "ranks": model.ranks}
+    for name, kw in (("tucker", {"tucker": model}), ("fp64_generated", {"entries": "fp64"})):
+        ph = []
+        for _ in range(args.warmup + args.steps):
+            vc = V.VoxCap(lab, w.conductor_id, w.eps_r, w.voxel_size, **kw)
+            ph.append(vc.setup_times())
+            vc.close()
+        out[name] = {k: statistics.median(p[k] for p in ph[args.warmup:]) for k in ph[0]}
+    return out
+
+
 # ---------------------------------------------------------------- the reference arm
 def run_reference(args, rank, world):
     """The oracle (plain FP64 CPU; the paper publishes no code) on the same
@@ -615,9 +639,14 @@ def main():
                     help="time only the batched FP32 products of the workload (profiling aid)")
     ap.add_argument("--path", type=int, default=-1,
                     help="with --products: FP32 product kernels 0 generic, 1 compiled plans, -1 tuned")
+    ap.add_argument("--setup", action="store_true",
+                    help="time only the set-up of the workload, Tucker-restored and generated (profiling aid)")
     args = ap.parse_args()
     if args.products:
         print(json.dumps(run_products(args)), flush=True)
+        return
+    if args.setup:
+        print(json.dumps(run_setup(args)), flush=True)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -40,7 +40,9 @@ __global__ void __launch_bounds__(NT) k_xfwd_fast(XArgs a, const float* __restri
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   C* tws = buf + L * PT;
+  C* phs = tws + twn;                 // half-voxel phases of the x grid
   fast::load_table<NT>(tws, stw, twn);
+  fast::load_table<NT>(phs, phx, H);
   const Geom& g = a.g;
   const int z = blockIdx.y;
   const int bg = blockIdx.z;                 // b * 3 + grid
@@ -77,7 +79,7 @@ __global__ void __launch_bounds__(NT) k_xfwd_fast(XArgs a, const float* __restri
     C A = cscale(cadd(zk, zc), 0.5f);
     C B = cscale(cmul_mi(csub(zk, zc)), 0.5f);
     if (grid == 0) {
-      const C ph = phx[k];
+      const C ph = phs[k];
       A = cmul(A, ph);
       B = cmul(B, ph);
     }
@@ -97,7 +99,9 @@ __global__ void __launch_bounds__(NT) k_xinv_fast(XArgs a, const C* __restrict__
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   C* tws = buf + L * PT;
+  C* phs = tws + twn;                 // half-voxel phases of the x grid
   fast::load_table<NT>(tws, stw, twn);
+  fast::load_table<NT>(phs, phx, H);
   const Geom& g = a.g;
   const int z = blockIdx.y;
   const int bo = blockIdx.z;                 // b * 3 + orientation
@@ -107,6 +111,7 @@ __global__ void __launch_bounds__(NT) k_xinv_fast(XArgs a, const C* __restrict__
   const int64_t plane = (int64_t)g.Ly * H;
   const C* srcA = in + (((int64_t)b * 6 + al) * g.Lz + z) * plane;        // potential
   const C* srcB = in + (((int64_t)b * 6 + 3 + al) * g.Lz + z) * plane;    // field
+  __syncthreads();                                                        // tables loaded
   // Hermitian extension of potential + i field, lanes along x
   for (int t = threadIdx.x; t < L * NL; t += NT) {
     const int l = t / L, k = t - l * L;
@@ -117,7 +122,7 @@ __global__ void __launch_bounds__(NT) k_xinv_fast(XArgs a, const C* __restrict__
       C A = srcA[ro];
       C B = srcB[ro];
       if (al == 0) {
-        const C ph = cconj(phx[kk]);
+        const C ph = cconj(phs[kk]);
         A = cmul(A, ph);
         B = cmul(B, ph);
       }
@@ -165,7 +170,7 @@ int launch_xfwd(const Handle& h, const float* x, C* out, int nrhs, cudaStream_t 
   const Geom& g = h.g;
   const Plan1D<float2>& p = h.pf[0];
   constexpr int L = R1 * R2 * R3;
-  const size_t sm = ((size_t)L * (NL + 1) + p.twn) * sizeof(C);
+  const size_t sm = ((size_t)L * (NL + 1) + p.twn + L / 2 + 1) * sizeof(C);
   auto kern = k_xfwd_fast<R1, R2, R3, NL, NT>;
   VC_TRY(set_smem(kern, sm));
   const int nlines = (g.Ly + 1) / 2;
@@ -183,7 +188,7 @@ int launch_xinv(const Handle& h, const C* in, const float* x, float* y, int nrhs
   const Geom& g = h.g;
   const Plan1D<float2>& p = h.pf[0];
   constexpr int L = R1 * R2 * R3;
-  const size_t sm = ((size_t)L * (NL + 1) + p.twn) * sizeof(C);
+  const size_t sm = ((size_t)L * (NL + 1) + p.twn + L / 2 + 1) * sizeof(C);
   auto kern = k_xinv_fast<R1, R2, R3, NL, NT>;
   VC_TRY(set_smem(kern, sm));
   const int B = h.pan.S * nrhs;

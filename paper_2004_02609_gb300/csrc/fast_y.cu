@@ -25,7 +25,9 @@ __global__ void __launch_bounds__(NT) k_ypass_fast(Geom g, int G, const C* __res
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   C* tws = buf + L * TX;
+  C* phs = tws + twn;                 // half-voxel phases of the y grid
   fast::load_table<NT>(tws, stw, twn);
+  fast::load_table<NT>(phs, phy, L);
   const int H = g.Hx;
   const int k0 = blockIdx.x * TX;
   const int z = blockIdx.y;
@@ -45,7 +47,7 @@ __global__ void __launch_bounds__(NT) k_ypass_fast(Geom g, int G, const C* __res
         C v = mk<C>(0.f, 0.f);
         if (c < ncol && y < Lin) {
           v = src[(int64_t)y * H + c];
-          if (INV && phase) v = cmul(v, cconj(phy[y]));
+          if (INV && phase) v = cmul(v, cconj(phs[y]));
         }
         return v;
       },
@@ -57,7 +59,7 @@ __global__ void __launch_bounds__(NT) k_ypass_fast(Geom g, int G, const C* __res
       tws + (P::NST == 3 ? off3 : off2), [&](int c, int pos) -> C { return buf[pos * TX + c]; },
       [&](int c, int y, C v) {
         if (c < ncol && y < Lout) {
-          if (!INV && phase) v = cmul(v, phy[y]);
+          if (!INV && phase) v = cmul(v, phs[y]);
           dst[(int64_t)y * H + c] = v;
         }
       });
@@ -68,7 +70,7 @@ int launch_y(const Handle& h, int G, const C* in, C* out, int64_t ibs, int64_t o
   const Geom& g = h.g;
   const Plan1D<float2>& p = h.pf[1];
   constexpr int L = R1 * R2 * R3;
-  const size_t sm = ((size_t)L * TX + p.twn) * sizeof(C);
+  const size_t sm = ((size_t)L * TX + p.twn + L) * sizeof(C);
   auto kern = k_ypass_fast<INV, R1, R2, R3, TX, NT>;
   VC_TRY(set_smem(kern, sm));
   dim3 grid((g.Hx + TX - 1) / TX, g.Lz, B * G);

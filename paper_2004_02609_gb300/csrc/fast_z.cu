@@ -9,8 +9,7 @@
 // input grids from HBM and fills the shared buffer [Mz][3][TX]; each thread
 // then holds the RB frequencies kz = j + RA r of its column for all three
 // grids (last forward stage, parked in a second shared buffer), multiplies
-// them with the kernel spectra -- read as one 64-byte record of the 15 real
-// kernels per frequency, side by side -- and runs the first inverse stage;
+// them with the real kernel spectra and runs the first inverse stage;
 // the outputs go through the first buffer in two halves (potential grids,
 // then field grids) to the last inverse stage (radix RA), which writes
 // planes z <= N_z to HBM.
@@ -47,20 +46,21 @@ constexpr int kidx(int half, int al, int be) {
 }
 
 // One output grid AL of half HALF at the thread's RB frequencies: the 3 RB
-// kernel values (read together from the 64-byte records), the fold signs,
+// kernel values (read together; consecutive columns of a warp read
+// consecutive floats of one kernel's octant), the fold signs,
 // the sum over the 3 source grids, the output half-voxel phase of z grids,
 // the first inverse stage, and the store to the line buffer.
 template <int HALF, int AL, int RA, int RB, int NT, int TX, int LD>
-__device__ __forceinline__ void mac_out(const float* __restrict__ specv, const int* off, bool col_ok, float sy,
-                                        const C* S, int t, int j, int c, const C* ph, C* buf) {
+__device__ __forceinline__ void mac_out(const float* __restrict__ spec, int otot, const int* off, bool col_ok,
+                                        float sy, const C* S, int t, int j, int c, const C* ph, C* buf) {
   constexpr int L = RA * RB;
   constexpr int K0 = kidx(HALF, AL, 0), K1 = kidx(HALF, AL, 1), K2 = kidx(HALF, AL, 2);
   float kv[RB][3];
 #pragma unroll
   for (int r = 0; r < RB; ++r) {
-    kv[r][0] = col_ok ? __ldg(specv + off[r] + K0) : 0.f;
-    kv[r][1] = col_ok ? __ldg(specv + off[r] + K1) : 0.f;
-    kv[r][2] = col_ok ? __ldg(specv + off[r] + K2) : 0.f;
+    kv[r][0] = col_ok ? __ldg(spec + K0 * otot + off[r]) : 0.f;
+    kv[r][1] = col_ok ? __ldg(spec + K1 * otot + off[r]) : 0.f;
+    kv[r][2] = col_ok ? __ldg(spec + K2 * otot + off[r]) : 0.f;
   }
   C o[RB];
 #pragma unroll
@@ -83,7 +83,7 @@ __device__ __forceinline__ void mac_out(const float* __restrict__ specv, const i
 
 template <int RA, int RB, int TX>
 __global__ void __launch_bounds__(RA * TX, 2) k_zpass_fast(Geom g, C* __restrict__ data,
-                                                          const float* __restrict__ specv,
+                                                          const float* __restrict__ spec, int otot,
                                                           const C* __restrict__ twf, int twn_f, int offB,
                                                           const C* __restrict__ twv, int twn_v, int offA,
                                                           const C* __restrict__ phz, int nbatch) {
@@ -140,8 +140,8 @@ __global__ void __launch_bounds__(RA * TX, 2) k_zpass_fast(Geom g, C* __restrict
   }
   __syncthreads();                                      // the buffer takes the outputs now
 
-  // frequency records of the column: (kz folded, ky folded, kx); 32-bit
-  // offsets (the launch checks that the records fit) computed once
+  // spectral index of the column's frequencies (kz folded, ky folded, kx)
+  // in a kernel's octant [Oz][Oy][Hx]; 32-bit (the launch checks the size)
   const int64_t q = q0 + c;
   const int ky = col_ok ? (int)(q / H) : 0;
   const int kx = col_ok ? (int)(q - (int64_t)ky * H) : 0;
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(RA * TX, 2) k_zpass_fast(Geom g, C* __restrict
 #pragma unroll
   for (int r = 0; r < RB; ++r) {
     const int kz = j + r * RA;
-    off[r] = ((kz > L / 2 ? L - kz : kz) * zrec + rec0) * 16;
+    off[r] = (kz > L / 2 ? L - kz : kz) * zrec + rec0;
   }
 
 #pragma unroll 1
@@ -161,14 +161,24 @@ __global__ void __launch_bounds__(RA * TX, 2) k_zpass_fast(Geom g, C* __restrict
     // potential outputs (half 0: kernels 0..5, Eq. 12 pairs shared) or
     // normal-field outputs (half 1: kernels 6..14, times -i), one output
     // grid at a time; the 3 RB kernel values of a grid are loaded together
+    // (the kernel stride passes through an opaque move and the empty asm
+    // statements separate the grids, so that the compiler neither hoists
+    // the 162 load addresses out of this loop nor one grid's loads into the
+    // previous grid's work: both would only cost registers)
+    int ot;
+    asm volatile("mov.b32 %0, %1;" : "=r"(ot) : "r"(otot));
     if (half == 0) {
-      mac_out<0, 0, RA, RB, NT, TX, LD>(specv, off, col_ok, sy, S, t, j, c, ph, buf);
-      mac_out<0, 1, RA, RB, NT, TX, LD>(specv, off, col_ok, sy, S, t, j, c, ph, buf);
-      mac_out<0, 2, RA, RB, NT, TX, LD>(specv, off, col_ok, sy, S, t, j, c, ph, buf);
+      mac_out<0, 0, RA, RB, NT, TX, LD>(spec, ot, off, col_ok, sy, S, t, j, c, ph, buf);
+      asm volatile("" ::: "memory");
+      mac_out<0, 1, RA, RB, NT, TX, LD>(spec, ot, off, col_ok, sy, S, t, j, c, ph, buf);
+      asm volatile("" ::: "memory");
+      mac_out<0, 2, RA, RB, NT, TX, LD>(spec, ot, off, col_ok, sy, S, t, j, c, ph, buf);
     } else {
-      mac_out<1, 0, RA, RB, NT, TX, LD>(specv, off, col_ok, sy, S, t, j, c, ph, buf);
-      mac_out<1, 1, RA, RB, NT, TX, LD>(specv, off, col_ok, sy, S, t, j, c, ph, buf);
-      mac_out<1, 2, RA, RB, NT, TX, LD>(specv, off, col_ok, sy, S, t, j, c, ph, buf);
+      mac_out<1, 0, RA, RB, NT, TX, LD>(spec, ot, off, col_ok, sy, S, t, j, c, ph, buf);
+      asm volatile("" ::: "memory");
+      mac_out<1, 1, RA, RB, NT, TX, LD>(spec, ot, off, col_ok, sy, S, t, j, c, ph, buf);
+      asm volatile("" ::: "memory");
+      mac_out<1, 2, RA, RB, NT, TX, LD>(spec, ot, off, col_ok, sy, S, t, j, c, ph, buf);
     }
     __syncthreads();
     // ---- last inverse stage (radix RA), buffer -> HBM, planes z < Lz
@@ -188,15 +198,14 @@ int launch_z(const Handle& h, C* data, int B, cudaStream_t st) {
   const Plan1D<float2>& pz = h.pzf[0];
   const Plan1D<float2>& pv = h.pzfr[0];
   constexpr int L = RA * RB;
-  VC_CHECK(h.spec_v.p != nullptr, VOXCAP_ERR_UNSUPPORTED, "interleaved spectra missing for the z pass");
   const size_t sm = ((size_t)L * 3 * TX + (size_t)3 * RB * RA * TX + pz.twn + pv.twn + L) * sizeof(C);
   const int64_t cols = (int64_t)g.My * g.Hx;
   const int64_t tiles = (cols + TX - 1) / TX;
-  VC_CHECK(tiles * B < ((int64_t)1 << 31) && (int64_t)g.Hx * g.Oy * g.Oz * 16 < ((int64_t)1 << 31),
+  VC_CHECK(tiles * B < ((int64_t)1 << 31) && (int64_t)g.Hx * g.Oy * g.Oz * kNumKernels < ((int64_t)1 << 31),
            VOXCAP_ERR_UNSUPPORTED, "grid too large for the compiled z pass");
   auto kern = k_zpass_fast<RA, RB, TX>;
   VC_TRY(set_smem(kern, sm));
-  kern<<<(unsigned)(tiles * B), RA * TX, sm, st>>>(g, data, h.spec_v.p, pz.stw,
+  kern<<<(unsigned)(tiles * B), RA * TX, sm, st>>>(g, data, h.spec_f.p, (int)((int64_t)g.Hx * g.Oy * g.Oz), pz.stw,
                                                    pz.twn, pz.twoff[1], pv.stw, pv.twn, pv.twoff[1], h.phf[2], B);
   ::vc::note_launch();
   VC_CUDA(cudaGetLastError());

@@ -221,8 +221,6 @@ struct Handle {
   DBuf<double> toep[kNumKernels];
   DBuf<double> spec_d;            // [15][Oz][Oy][Hx] real, scaled by 1/(Mx My Mz)
   DBuf<float> spec_f;
-  DBuf<float> spec_v;             // [Oz][Oy][Hx][16] FP32: the 15 kernels of a frequency side by
-                                  // side (16th zero), read by the compiled z pass
   // MVM workspace
   int ws_batch = 0;
   DBuf<char> ws;                  // raw workspace

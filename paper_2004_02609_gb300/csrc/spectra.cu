@@ -18,7 +18,6 @@
 #include <cstring>
 #include <vector>
 
-#include "fast.cuh"
 #include "internal.h"
 
 namespace vc {
@@ -478,25 +477,6 @@ static int spectra_impl(Handle& h) {
   return VOXCAP_OK;
 }
 
-// spec_v[t][kk] = spec_f[kk][t] (kk < 15), spec_v[t][15] = 0
-__global__ void k_interleave(const float* __restrict__ Rf, int64_t Otot, float* __restrict__ Rv) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= Otot * 16) return;
-  const int kk = (int)(t & 15);
-  Rv[t] = kk < kNumKernels ? Rf[(int64_t)kk * Otot + (t >> 4)] : 0.0f;
-}
-
-int build_spectra(Handle& h) {
-  VC_TRY(h.far32 ? spectra_impl<float>(h) : spectra_impl<double>(h));
-  if (fast_z_ok(h)) {
-    const Geom& g = h.g;
-    const int64_t Otot = (int64_t)g.Hx * g.Oy * g.Oz;
-    VC_TRY(h.spec_v.alloc((size_t)Otot * 16));
-    k_interleave<<<(unsigned)((Otot * 16 + 255) / 256), 256, 0, h.stream>>>(h.spec_f.p, Otot, h.spec_v.p);
-    ::vc::note_launch();
-    VC_CUDA(cudaGetLastError());
-  }
-  return VOXCAP_OK;
-}
+int build_spectra(Handle& h) { return h.far32 ? spectra_impl<float>(h) : spectra_impl<double>(h); }
 
 }  // namespace vc

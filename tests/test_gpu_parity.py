@@ -297,6 +297,34 @@ def test_matvec_compiled_plans(n, axis):
     assert vc.set_product_path(-1) in (0, 1)
 
 
+@pytest.mark.parametrize("shape", [(17, 16, 17), (35, 17, 16)])
+def test_matvec_compiled_plans_every_axis(shape):
+    """Compiled x, y and z passes together (every padded length 36 or 72):
+    forward and transposed FP32 products against the dense oracle, two
+    columns, on two conductors in opposite corners of the grid, one with a
+    dielectric cap."""
+    import torch
+    nx, ny, nz = shape
+    lab = np.zeros((nz, ny, nx), np.int32)
+    lab[2:5, 2:5, 2:5] = 2                      # conductor 0
+    lab[2:5, 2:5, 5:7] = 1                      # dielectric cap, eps_r 4
+    lab[nz - 5:nz - 2, ny - 5:ny - 2, nx - 5:nx - 2] = 3    # conductor 1, far corner
+    w = W.Workload(f"corners{shape}", lab, np.array([-1, -1, 0, 1], np.int32), np.array([1.0, 4.0, 1.0, 1.0]))
+    vc = make(w)
+    assert all(M in (36, 72) for M in vc.fft_lengths()), vc.fft_lengths()
+    ps, A = dense(w)
+    X = np.random.default_rng(13).standard_normal((2, ps.n))
+    x32 = torch.tensor(X, device="cuda", dtype=torch.float32)
+    for path in (1, 0):
+        assert vc.set_product_path(path) == path
+        for rep in range(2):
+            f = vc.matvec(x32).cpu().numpy()
+            t = vc.matvec(x32, adjoint=True).cpu().numpy()
+            for r in range(2):
+                assert rel_l2(f[r], A @ X[r]) < 2e-6, (path, rep, r)
+                assert rel_l2(t[r], A.T @ X[r]) < 2e-6, (path, rep, r)
+
+
 def test_matvec_paper_padding_equals_smooth_padding():
     """Any padded length >= 2N+1 gives the same linear convolution (Appendix B):
     the paper's 2(N+1) and the smooth length agree to rounding."""
