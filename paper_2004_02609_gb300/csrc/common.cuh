@@ -110,9 +110,18 @@ template <typename C> __device__ __forceinline__ C cmul_i(C a, bool inv) {   // 
   return inv ? cmul_pi(a) : cmul_mi(a);
 }
 
-template <int R, typename C> __device__ __forceinline__ void dft(C* v, bool inv) {
+// HIN: only v[0 .. R/2) are given, the upper half of the inputs is zero (a
+// zero-padded line's first stage); even R only.
+template <int R, typename C, bool HIN = false> __device__ __forceinline__ void dft(C* v, bool inv) {
   using T = decltype(C::x);
-  if constexpr (R == 2) {
+  static_assert(!HIN || R == 2 || R == 4 || R == 8 || R == 16, "half-input DFT of an even radix only");
+  if constexpr (R == 2 && HIN) {
+    v[1] = v[0];
+  } else if constexpr (R == 4 && HIN) {
+    const C a = v[0], b = v[1], bi = cmul_i(b, inv);
+    v[0] = cadd(a, b); v[2] = csub(a, b);
+    v[1] = cadd(a, bi); v[3] = csub(a, bi);
+  } else if constexpr (R == 2) {
     C a = v[0], b = v[1];
     v[0] = cadd(a, b); v[1] = csub(a, b);
   } else if constexpr (R == 3) {
@@ -165,8 +174,8 @@ template <int R, typename C> __device__ __forceinline__ void dft(C* v, bool inv)
 #pragma unroll
     for (int k1 = 0; k1 < Q; ++k1) {
 #pragma unroll
-      for (int n2 = 0; n2 < Q; ++n2) a[k1][n2] = v[k1 + Q * n2];
-      dft<Q, C>(a[k1], inv);
+      for (int n2 = 0; n2 < Q; ++n2) a[k1][n2] = (HIN && n2 >= Q / 2) ? mk<C>(0, 0) : v[k1 + Q * n2];
+      dft<Q, C, HIN>(a[k1], inv);
     }
 #pragma unroll
     for (int k1 = 1; k1 < Q; ++k1)
@@ -201,10 +210,10 @@ template <int R, typename C> __device__ __forceinline__ void dft(C* v, bool inv)
     }
   } else {   // R == 8: two radix-4 halves
     using TT = T;
-    C e[4] = {v[0], v[2], v[4], v[6]};
-    C o[4] = {v[1], v[3], v[5], v[7]};
-    dft<4, C>(e, inv);
-    dft<4, C>(o, inv);
+    C e[4] = {v[0], v[2], HIN ? mk<C>(0, 0) : v[4], HIN ? mk<C>(0, 0) : v[6]};
+    C o[4] = {v[1], v[3], HIN ? mk<C>(0, 0) : v[5], HIN ? mk<C>(0, 0) : v[7]};
+    dft<4, C, HIN>(e, inv);
+    dft<4, C, HIN>(o, inv);
     const TT h = (TT)0.70710678118654752440084436210484903928;
     C w1 = inv ? mk<C>(h, h) : mk<C>(h, -h);
     C o1 = cmul(o[1], w1);

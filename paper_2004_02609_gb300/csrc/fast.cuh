@@ -41,9 +41,14 @@ __device__ __forceinline__ void twiddle(C* v, const C* __restrict__ tw, int k) {
 // NT threads.  ld(c, pos) gives the input, st(c, pos, v) takes the output.
 // All inputs of a thread's butterflies are loaded before any is transformed,
 // so that a stage reading HBM keeps all of its loads in flight at once.
-template <int L, int R, int NS, int TX, int NT, bool INV, typename Ld, typename St>
+// RIN = R / 2 (first stage only): inputs at positions >= L / 2 are the zero
+// padding, neither read nor added.  ROUT < R: only outputs r < ROUT of a
+// butterfly are needed (the last stage of a transform whose result is cut to
+// fewer than L / 2 positions); the others are not computed.
+template <int L, int R, int NS, int TX, int NT, bool INV, int RIN = R, int ROUT = R, typename Ld, typename St>
 __device__ __forceinline__ void stage(const C* __restrict__ tw, Ld ld, St st) {
   constexpr int NB = L / R, TOT = NB * TX, IT = (TOT + NT - 1) / NT;
+  static_assert(RIN == R || (RIN * 2 == R && NS == 1), "half inputs in a first stage only");
   C v[IT][R];
 #pragma unroll
   for (int it = 0; it < IT; ++it) {
@@ -51,7 +56,7 @@ __device__ __forceinline__ void stage(const C* __restrict__ tw, Ld ld, St st) {
     if (TOT % NT == 0 || item < TOT) {
       const int c = item % TX, j = item / TX;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[it][r] = ld(c, j + r * NB);
+      for (int r = 0; r < RIN; ++r) v[it][r] = ld(c, j + r * NB);
     }
   }
 #pragma unroll
@@ -60,10 +65,10 @@ __device__ __forceinline__ void stage(const C* __restrict__ tw, Ld ld, St st) {
     if (TOT % NT == 0 || item < TOT) {
       const int c = item % TX, j = item / TX, k = j % NS;
       if (NS > 1) twiddle<R, INV>(v[it], tw, k);
-      dft<R, C>(v[it], INV);
+      dft<R, C, (RIN < R)>(v[it], INV);
       const int base = (j - k) * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) st(c, base + r * NS, v[it][r]);
+      for (int r = 0; r < ROUT; ++r) st(c, base + r * NS, v[it][r]);
     }
   }
 }
@@ -71,9 +76,10 @@ __device__ __forceinline__ void stage(const C* __restrict__ tw, Ld ld, St st) {
 // The same stage in place on buf (element (pos, c) at pos * PT + c, pitch
 // PT >= TX): all inputs of a thread's butterflies are read, the block
 // synchronises, the outputs are written, and the block synchronises again.
-template <int L, int R, int NS, int TX, int NT, bool INV, int PT = TX>
+template <int L, int R, int NS, int TX, int NT, bool INV, int PT = TX, int RIN = R, int ROUT = R>
 __device__ __forceinline__ void stage_inplace(C* buf, const C* __restrict__ tw) {
   constexpr int NB = L / R, TOT = NB * TX, IT = (TOT + NT - 1) / NT;
+  static_assert(RIN == R || (RIN * 2 == R && NS == 1), "half inputs in a first stage only");
   C v[IT][R];
 #pragma unroll
   for (int it = 0; it < IT; ++it) {
@@ -81,7 +87,7 @@ __device__ __forceinline__ void stage_inplace(C* buf, const C* __restrict__ tw) 
     if (TOT % NT == 0 || item < TOT) {
       const int c = item % TX, j = item / TX;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[it][r] = buf[(j + r * NB) * PT + c];
+      for (int r = 0; r < RIN; ++r) v[it][r] = buf[(j + r * NB) * PT + c];
     }
   }
   __syncthreads();
@@ -91,22 +97,31 @@ __device__ __forceinline__ void stage_inplace(C* buf, const C* __restrict__ tw) 
     if (TOT % NT == 0 || item < TOT) {
       const int c = item % TX, j = item / TX, k = j % NS;
       if (NS > 1) twiddle<R, INV>(v[it], tw, k);
-      dft<R, C>(v[it], INV);
+      dft<R, C, (RIN < R)>(v[it], INV);
       const int base = (j - k) * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) buf[(base + r * NS) * PT + c] = v[it][r];
+      for (int r = 0; r < ROUT; ++r) buf[(base + r * NS) * PT + c] = v[it][r];
     }
   }
   __syncthreads();
 }
 
 // A whole transform of TX interleaved lines held in buf, every stage in
-// place (twiddle tables of the plan's stages at tw + off[s]).
-template <typename P, int TX, int NT, bool INV, int PT = TX>
+// place (twiddle tables of the plan's stages at tw + off[s]).  HIN: the
+// input lines are zero from position L / 2 on (those entries of buf are
+// never read); HOUT: only positions < L / 2 of the result are used (the
+// last stage leaves the others unwritten).
+template <typename P, int TX, int NT, bool INV, int PT = TX, bool HIN = false, bool HOUT = false>
 __device__ __forceinline__ void transform_inplace(C* buf, const C* __restrict__ tw, int off2, int off3) {
-  stage_inplace<P::L, P::R1, 1, TX, NT, INV, PT>(buf, tw);
-  stage_inplace<P::L, P::R2, P::R1, TX, NT, INV, PT>(buf, tw + off2);
-  if constexpr (P::NST == 3) stage_inplace<P::L, P::R3, P::R1 * P::R2, TX, NT, INV, PT>(buf, tw + off3);
+  constexpr int RL = P::NST == 3 ? P::R3 : P::R2;
+  constexpr int ROUT = HOUT ? (RL + 1) / 2 : RL;
+  stage_inplace<P::L, P::R1, 1, TX, NT, INV, PT, HIN ? P::R1 / 2 : P::R1>(buf, tw);
+  if constexpr (P::NST == 3) {
+    stage_inplace<P::L, P::R2, P::R1, TX, NT, INV, PT>(buf, tw + off2);
+    stage_inplace<P::L, P::R3, P::R1 * P::R2, TX, NT, INV, PT, P::R3, ROUT>(buf, tw + off3);
+  } else {
+    stage_inplace<P::L, P::R2, P::R1, TX, NT, INV, PT, P::R2, ROUT>(buf, tw + off2);
+  }
 }
 
 // copy n complex values to shared memory (caller synchronises)

@@ -13,6 +13,9 @@
 // the potential, a dielectric row I' x + the field (Eq. 4).
 // NL lines share one shared-memory buffer with a pitch of NL + 1 complex
 // values, so that reads along x by consecutive lanes avoid bank conflicts.
+// The padded length is at least twice the row length: the forward transform
+// reads only the lower half of its first stage's inputs, and the inverse
+// one computes only the outputs below L / 2.
 #include "fast.cuh"
 
 namespace vc {
@@ -51,7 +54,7 @@ __global__ void __launch_bounds__(NT) k_xfwd_fast(XArgs a, const float* __restri
   const int nlines = (g.Ly + 1) / 2;         // two rows per complex line
   const int l0 = blockIdx.x * NL;
   const float* xr = x + (int64_t)r * a.N;
-  for (int i = threadIdx.x; i < L * PT; i += NT) buf[i] = mk<C>(0.f, 0.f);
+  for (int i = threadIdx.x; i < (L / 2) * PT; i += NT) buf[i] = mk<C>(0.f, 0.f);   // the upper half is never read
   __syncthreads();
   // scatter: one warp per row (2 NL rows), lanes over the row's panels
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -69,7 +72,7 @@ __global__ void __launch_bounds__(NT) k_xfwd_fast(XArgs a, const float* __restri
     }
   }
   __syncthreads();
-  fast::transform_inplace<P, NL, NT, false, PT>(buf, tws, off2, off3);
+  fast::transform_inplace<P, NL, NT, false, PT, true, false>(buf, tws, off2, off3);
   // split the two rows' half spectra, phase of the x grid, store
   for (int t = threadIdx.x; t < H * NL; t += NT) {
     const int l = t / H, k = t - l * H;
@@ -112,30 +115,44 @@ __global__ void __launch_bounds__(NT) k_xinv_fast(XArgs a, const C* __restrict__
   const C* srcA = in + (((int64_t)b * 6 + al) * g.Lz + z) * plane;        // potential
   const C* srcB = in + (((int64_t)b * 6 + 3 + al) * g.Lz + z) * plane;    // field
   __syncthreads();                                                        // tables loaded
-  // Hermitian extension of potential + i field, lanes along x
-  for (int t = threadIdx.x; t < L * NL; t += NT) {
-    const int l = t / L, k = t - l * L;
-    C v = mk<C>(0.f, 0.f);
-    if (l0 + l < g.Ly) {
-      const int kk = k <= L / 2 ? k : L - k;
-      const int64_t ro = (int64_t)(l0 + l) * H + kk;
-      C A = srcA[ro];
-      C B = srcB[ro];
-      if (al == 0) {
-        const C ph = cconj(phs[kk]);
-        A = cmul(A, ph);
-        B = cmul(B, ph);
+  // Hermitian extension of potential + i field, lanes along x: each half-
+  // spectrum value k is read once and gives line entries k and L - k; the
+  // loads of U items are issued before any of them is used
+  constexpr int TOT = H * NL, IT = (TOT + NT - 1) / NT, U = 6;
+#pragma unroll
+  for (int i0 = 0; i0 < IT; i0 += U) {
+    C A[U], B[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int t = (i0 + u) * NT + (int)threadIdx.x;
+      A[u] = B[u] = mk<C>(0.f, 0.f);
+      if (i0 + u < IT && t < TOT) {
+        const int l = t / H, k = t - l * H;
+        if (l0 + l < g.Ly) {
+          const int64_t ro = (int64_t)(l0 + l) * H + k;
+          A[u] = srcA[ro];
+          B[u] = srcB[ro];
+        }
       }
-      if (k > L / 2) {
-        A = cconj(A);
-        B = cconj(B);
-      }
-      v = cadd(A, cmul_pi(B));
     }
-    buf[k * PT + l] = v;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int t = (i0 + u) * NT + (int)threadIdx.x;
+      if (i0 + u < IT && t < TOT) {
+        const int l = t / H, k = t - l * H;
+        C a = A[u], b = B[u];
+        if (al == 0) {
+          const C ph = cconj(phs[k]);
+          a = cmul(a, ph);
+          b = cmul(b, ph);
+        }
+        buf[k * PT + l] = cadd(a, cmul_pi(b));
+        if (k > 0 && k < L / 2) buf[(L - k) * PT + l] = cadd(cconj(a), cmul_pi(cconj(b)));
+      }
+    }
   }
   __syncthreads();
-  fast::transform_inplace<P, NL, NT, true, PT>(buf, tws, off2, off3);
+  fast::transform_inplace<P, NL, NT, true, PT, false, true>(buf, tws, off2, off3);
   // gather at the panels of each row: one warp per row
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const float* xr = x + (int64_t)r * a.N;
@@ -171,6 +188,7 @@ int launch_xfwd(const Handle& h, const float* x, C* out, int nrhs, cudaStream_t 
   const Plan1D<float2>& p = h.pf[0];
   constexpr int L = R1 * R2 * R3;
   const size_t sm = ((size_t)L * (NL + 1) + p.twn + L / 2 + 1) * sizeof(C);
+  VC_CHECK(2 * g.Lx <= L, VOXCAP_ERR_UNSUPPORTED, "x padding shorter than twice the grid");
   auto kern = k_xfwd_fast<R1, R2, R3, NL, NT>;
   VC_TRY(set_smem(kern, sm));
   const int nlines = (g.Ly + 1) / 2;
@@ -189,6 +207,7 @@ int launch_xinv(const Handle& h, const C* in, const float* x, float* y, int nrhs
   const Plan1D<float2>& p = h.pf[0];
   constexpr int L = R1 * R2 * R3;
   const size_t sm = ((size_t)L * (NL + 1) + p.twn + L / 2 + 1) * sizeof(C);
+  VC_CHECK(2 * g.Lx <= L, VOXCAP_ERR_UNSUPPORTED, "x padding shorter than twice the grid");
   auto kern = k_xinv_fast<R1, R2, R3, NL, NT>;
   VC_TRY(set_smem(kern, sm));
   const int B = h.pan.S * nrhs;

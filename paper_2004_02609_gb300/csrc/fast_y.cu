@@ -3,10 +3,15 @@
 // are the padding and are not read) and the inverse transform back to the
 // N_y+1 rows the panels need, with the half-voxel phase of the y grids.
 //
-// A CTA transforms TX = 16 consecutive kx columns (128-byte row segments) of
-// one z plane of one grid: the first stage reads HBM into registers and
-// writes the one shared-memory buffer, a middle stage runs in place, and the
-// last stage writes HBM from registers.
+// A CTA transforms TX consecutive lines of the flattened (z, kx) index of
+// one grid (128- or 64-byte row segments; a tile may run from the end of one
+// z plane into the next, so that no tile is left with a ragged remainder of
+// a row): the first stage reads HBM into registers and writes the one
+// shared-memory buffer, a middle stage runs in place, and the last stage
+// writes HBM from registers.  The padded length is at least twice the
+// unpadded one, so the forward first stage reads only the lower half of its
+// butterfly inputs and the inverse last stage computes only the outputs
+// below L / 2.
 #include "fast.cuh"
 
 namespace vc {
@@ -22,6 +27,7 @@ __global__ void __launch_bounds__(NT) k_ypass_fast(Geom g, int G, const C* __res
                                                    const C* __restrict__ phy) {
   using P = fast::Plan<R1, R2, R3>;
   constexpr int L = P::L;
+  static_assert(NT % TX == 0, "a thread keeps one line of the tile in every stage");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   C* tws = buf + L * TX;
@@ -29,24 +35,26 @@ __global__ void __launch_bounds__(NT) k_ypass_fast(Geom g, int G, const C* __res
   fast::load_table<NT>(tws, stw, twn);
   fast::load_table<NT>(phs, phy, L);
   const int H = g.Hx;
-  const int k0 = blockIdx.x * TX;
-  const int z = blockIdx.y;
-  const int bg = blockIdx.z;
+  const int bg = blockIdx.y;
   const int grid = bg % G, b = bg / G;
   const bool phase = (grid % 3) == 1;
   const int Lin = INV ? L : g.Ly;
   const int Lout = INV ? g.Ly : L;
-  const int ncol = min(TX, H - k0);
-  const C* src = in + (int64_t)b * in_bstride + ((int64_t)grid * g.Lz + z) * ((int64_t)Lin * H) + k0;
-  C* dst = out + (int64_t)b * out_bstride + ((int64_t)grid * g.Lz + z) * ((int64_t)Lout * H) + k0;
+  // this thread's line: q = z * H + kx
+  const int64_t q = (int64_t)blockIdx.x * TX + (int)threadIdx.x % TX;
+  const bool ok = q < (int64_t)g.Lz * H;
+  const int z = ok ? (int)(q / H) : 0;
+  const int kx = ok ? (int)(q - (int64_t)z * H) : 0;
+  const C* src = in + (int64_t)b * in_bstride + ((int64_t)grid * g.Lz + z) * ((int64_t)Lin * H) + kx;
+  C* dst = out + (int64_t)b * out_bstride + ((int64_t)grid * g.Lz + z) * ((int64_t)Lout * H) + kx;
   __syncthreads();
   // first stage: HBM -> registers -> buffer
-  fast::stage<L, R1, 1, TX, NT, INV>(
+  fast::stage<L, R1, 1, TX, NT, INV, INV ? R1 : R1 / 2>(
       tws,
-      [&](int c, int y) -> C {
+      [&](int, int y) -> C {
         C v = mk<C>(0.f, 0.f);
-        if (c < ncol && y < Lin) {
-          v = src[(int64_t)y * H + c];
+        if (ok && y < Lin) {
+          v = src[(int64_t)y * H];
           if (INV && phase) v = cmul(v, cconj(phs[y]));
         }
         return v;
@@ -55,12 +63,12 @@ __global__ void __launch_bounds__(NT) k_ypass_fast(Geom g, int G, const C* __res
   __syncthreads();
   if constexpr (P::NST == 3) fast::stage_inplace<L, R2, R1, TX, NT, INV>(buf, tws + off2);
   // last stage: buffer -> registers -> HBM
-  fast::stage<L, P::RL, P::NSL, TX, NT, INV>(
+  fast::stage<L, P::RL, P::NSL, TX, NT, INV, P::RL, INV ? (P::RL + 1) / 2 : P::RL>(
       tws + (P::NST == 3 ? off3 : off2), [&](int c, int pos) -> C { return buf[pos * TX + c]; },
-      [&](int c, int y, C v) {
-        if (c < ncol && y < Lout) {
+      [&](int, int y, C v) {
+        if (ok && y < Lout) {
           if (!INV && phase) v = cmul(v, phs[y]);
-          dst[(int64_t)y * H + c] = v;
+          dst[(int64_t)y * H] = v;
         }
       });
 }
@@ -73,7 +81,10 @@ int launch_y(const Handle& h, int G, const C* in, C* out, int64_t ibs, int64_t o
   const size_t sm = ((size_t)L * TX + p.twn + L) * sizeof(C);
   auto kern = k_ypass_fast<INV, R1, R2, R3, TX, NT>;
   VC_TRY(set_smem(kern, sm));
-  dim3 grid((g.Hx + TX - 1) / TX, g.Lz, B * G);
+  VC_CHECK(2 * g.Ly <= L, VOXCAP_ERR_UNSUPPORTED, "y padding shorter than twice the grid");
+  const int64_t tiles = ((int64_t)g.Lz * g.Hx + TX - 1) / TX;
+  VC_CHECK(tiles < ((int64_t)1 << 31) && B * G <= 65535, VOXCAP_ERR_UNSUPPORTED, "grid too large for the y pass");
+  dim3 grid((unsigned)tiles, B * G);
   kern<<<grid, NT, sm, st>>>(g, G, in, out, ibs, obs, p.stw, p.twn, p.twoff[1], p.nst >= 3 ? p.twoff[2] : 0,
                              h.phf[1]);
   ::vc::note_launch();
