@@ -407,15 +407,22 @@ int voxcap_setup_times(const voxcap_t* h, double* seconds);
  *  path 0   the generic passes (any padded length; the FP64 products always
  *           use them);
  *  path 1   passes compiled for fixed radix plans wherever the padded length
- *           of an axis has one (y: 36, 72, 144, 288, 576, 1152; z: 36, 72,
- *           144; forward z pass only), the generic passes elsewhere;
- *  path -1  re-run the set-up autotuner, which times both on this handle's
- *           own products and keeps the faster (cached per device, grid and
- *           batch);
+ *           of an axis has one (x and y: 36, 72, 144, 288, 576, 1152; z: 36,
+ *           72, 144; forward z pass only), the generic passes elsewhere, each
+ *           in its default launch variant;
+ *  path 1 + variant bits: 2 = the persistent z pass with asynchronous
+ *           prefetch of the next tile (z length 144), 4 / 8 = the narrower
+ *           tiles of the forward / inverse y pass (y length 1152); a bit
+ *           that does not apply to the handle's lengths changes nothing.
+ *           The variants of path 1 differ in tiling only: every line is
+ *           transformed with the same arithmetic, so they give the same bits;
+ *  path -1  re-run the set-up autotuner, which times the generic variants,
+ *           path 1 and its variant bits on this handle's own products and
+ *           keeps the fastest (cached per device, grid and batch);
  *  path -2  change nothing (query).
- *  path_out (may be NULL) receives the path in force.  Returns
- * VOXCAP_ERR_ARG for a NULL handle or a path outside -2..1.  Not safe while
- * another call on the same handle runs.
+ *  path_out (may be NULL) receives the path in force, with its variant bits.
+ * Returns VOXCAP_ERR_ARG for a NULL handle or a path outside -2..15 or even
+ * and above 1.  Not safe while another call on the same handle runs.
  */
 int voxcap_set_product_path(voxcap_t* h, int path, int* path_out);
 

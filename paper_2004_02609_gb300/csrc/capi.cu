@@ -324,7 +324,8 @@ int voxcap_setup_times(const voxcap_t* hv, double* seconds) {
 
 int voxcap_set_product_path(voxcap_t* hv, int path, int* path_out) {
   VC_CHECK(hv != nullptr, VOXCAP_ERR_ARG, "NULL handle");
-  VC_CHECK(path >= -2 && path <= 1, VOXCAP_ERR_ARG, "path must be -2, -1, 0 or 1");
+  VC_CHECK(path >= -2 && path <= 15 && (path <= 1 || (path & 1)), VOXCAP_ERR_ARG,
+           "path must be -2, -1, 0, 1 or 1 plus variant bits 2, 4, 8");
   Handle& h = hv->h;
   set_alloc_stream(h.stream);
   if (path == -2) {
@@ -332,10 +333,12 @@ int voxcap_set_product_path(voxcap_t* hv, int path, int* path_out) {
   } else if (path < 0) {
     VC_TRY(retune_products(h));
   } else {
-    h.path = path;
-    h.yvar = 0;
+    h.path = path & 1;
+    h.zfvar = (path >> 1) & 1;
+    h.yvar[0] = (path >> 2) & 1;
+    h.yvar[1] = (path >> 3) & 1;
   }
-  if (path_out) *path_out = h.path;
+  if (path_out) *path_out = h.path == 1 ? 1 | (h.zfvar << 1) | (h.yvar[0] << 2) | (h.yvar[1] << 3) : h.path;
   return VOXCAP_OK;
 }
 

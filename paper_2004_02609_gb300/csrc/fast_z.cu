@@ -5,14 +5,32 @@
 // the inverse z transforms back to the N_z+1 planes the panels need.
 //
 // A CTA (RA * TX threads) takes TX consecutive (ky, kx) columns of one batch
-// item.  Stage A (radix RA) reads the N_z+1 non-zero planes of the three
-// input grids from HBM and fills the shared buffer [Mz][3][TX]; each thread
+// item, the rows ky taken in the order 0, 1, My-1, 2, My-2, ... so that the
+// two rows that share a folded row of the kernel spectra (ky and My-ky) run
+// back to back and the second reads the spectra from L2.  Stage A (radix RA,
+// only its lower RA/2 inputs: planes z >= Mz/2 are padding) reads the N_z+1
+// non-zero planes of the three input grids from HBM and fills the shared
+// buffer [Mz][3][TX]; each thread
 // then holds the RB frequencies kz = j + RA r of its column for all three
 // grids (last forward stage, parked in a second shared buffer), multiplies
 // them with the real kernel spectra and runs the first inverse stage;
 // the outputs go through the first buffer in two halves (potential grids,
 // then field grids) to the last inverse stage (radix RA), which writes
-// planes z <= N_z to HBM.
+// planes z <= N_z to HBM (only the outputs below Mz/2 are computed).
+//
+// k_zpass_pipe (Mz = 16 * 9, TX = 8) is the persistent form of the same
+// pass: a CTA loops over tiles, and while it works on one tile the next
+// tile's input planes arrive in a staging buffer by cp.async, so that
+// stage A reads shared memory instead of waiting on HBM.  Each thread keeps
+// its 27 charge spectra in registers (no second buffer: three CTAs fit an
+// SM), loads the kernel values of the next output grid while it computes
+// the current one, and folds the fold signs of Eq. 12's real spectra into
+// the charge and result spectra: with s_y, s_z = -1 on the mirrored half of
+// the y or z frequencies and s_x = 1, the sign of potential block P^{ab} is
+// s_a s_b and that of field block E^{ab} is s_b, so the sources are scaled
+// by s_b once and the potential results by s_a.
+#include <algorithm>
+
 #include "fast.cuh"
 
 namespace vc {
@@ -81,11 +99,17 @@ __device__ __forceinline__ void mac_out(const float* __restrict__ spec, int otot
   for (int r = 0; r < RB; ++r) buf[(j * RB + r) * LD + AL * TX + c] = o[r];
 }
 
+// Row i of the processing order: 0, 1, My-1, 2, My-2, ..., My/2 (My even).
+__device__ __forceinline__ int row_of(int i, int My) {
+  const int p = (i + 1) >> 1;
+  return (i & 1) || i == 0 ? p : My - p;
+}
+
 template <int RA, int RB, int TX>
 __global__ void __launch_bounds__(RA * TX, 2) k_zpass_fast(Geom g, C* __restrict__ data,
                                                           const float* __restrict__ spec, int otot,
                                                           const C* __restrict__ twf, int twn_f, int offB,
-                                                          const C* __restrict__ twv, int twn_v, int offA,
+                                                          const C* __restrict__ twv, int twn_v, int offA_tw,
                                                           const C* __restrict__ phz, int nbatch) {
   constexpr int L = RA * RB;
   constexpr int NT = RA * TX;
@@ -96,26 +120,36 @@ __global__ void __launch_bounds__(RA * TX, 2) k_zpass_fast(Geom g, C* __restrict
   C* tf = S + 3 * RB * NT;
   C* tv = tf + twn_f;
   C* ph = tv + twn_v;
+  int* colz = reinterpret_cast<int*>(ph + L);   // [TX] column offset in a z plane (ky H + kx)
+  int* coly = colz + TX;                        // [TX] its row ky
   fast::load_table<NT>(tf, twf, twn_f);
   fast::load_table<NT>(tv, twv, twn_v);
   fast::load_table<NT>(ph, phz, L);
   const int H = g.Hx;
   const int b = blockIdx.x % nbatch;                      // batch items of a tile run together
   const int64_t zstride = (int64_t)g.My * H;              // one z plane [My][H]
-  const int64_t q0 = (int64_t)(blockIdx.x / nbatch) * TX; // first column q = ky * H + kx
+  // first column of the tile in the processing order (rows by row_of)
+  const int64_t q0 = (int64_t)(blockIdx.x / nbatch) * TX;
   const int64_t gstride = (int64_t)g.Lz * zstride;
-  C* base = data + (int64_t)b * 6 * gstride + q0;
+  C* base = data + (int64_t)b * 6 * gstride;
   const int ncol = (int)min((int64_t)TX, zstride - q0);
+  if (threadIdx.x < TX) {
+    const int qq = (int)q0 + (int)threadIdx.x;                // < My H < 2^31 (checked at launch)
+    const int i = qq / H, kx = qq - i * H;
+    const int ky = threadIdx.x < ncol ? row_of(i, g.My) : 0;
+    coly[threadIdx.x] = ky;
+    colz[threadIdx.x] = threadIdx.x < ncol ? ky * H + kx : 0;
+  }
   const int Lz = g.Lz;
   __syncthreads();
 
   // ---- stage A: forward radix RA of the three input grids, HBM -> buffer
-  fast::stage<L, RA, 1, LD, NT, false>(
+  fast::stage<L, RA, 1, LD, NT, false, RA / 2>(
       tf,
       [&](int line, int z) -> C {
         const int grid = line / TX, c = line % TX;
         C v = mk<C>(0.f, 0.f);
-        if (c < ncol && z < Lz) v = base[grid * gstride + z * zstride + c];
+        if (c < ncol && z < Lz) v = base[grid * gstride + z * zstride + colz[c]];
         return v;
       },
       [&](int line, int pos, C v) { buf[pos * LD + line] = v; });
@@ -142,9 +176,8 @@ __global__ void __launch_bounds__(RA * TX, 2) k_zpass_fast(Geom g, C* __restrict
 
   // spectral index of the column's frequencies (kz folded, ky folded, kx)
   // in a kernel's octant [Oz][Oy][Hx]; 32-bit (the launch checks the size)
-  const int64_t q = q0 + c;
-  const int ky = col_ok ? (int)(q / H) : 0;
-  const int kx = col_ok ? (int)(q - (int64_t)ky * H) : 0;
+  const int ky = coly[c];
+  const int kx = colz[c] - ky * H;
   const bool fy = ky > g.My / 2;
   const float sy = fy ? -1.f : 1.f;
   const int rec0 = (fy ? g.My - ky : ky) * H + kx;
@@ -182,14 +215,238 @@ __global__ void __launch_bounds__(RA * TX, 2) k_zpass_fast(Geom g, C* __restrict
     }
     __syncthreads();
     // ---- last inverse stage (radix RA), buffer -> HBM, planes z < Lz
-    fast::stage<L, RA, RB, LD, NT, true>(
-        tv + offA, [&](int line, int pos) -> C { return buf[pos * LD + line]; },
+    fast::stage<L, RA, RB, LD, NT, true, RA, RA / 2>(
+        tv + offA_tw, [&](int line, int pos) -> C { return buf[pos * LD + line]; },
         [&](int line, int z, C v) {
           const int grid = line / TX + 3 * half, cc = line % TX;
-          if (cc < ncol && z < Lz) base[grid * gstride + z * zstride + cc] = v;
+          if (cc < ncol && z < Lz) base[grid * gstride + z * zstride + colz[cc]] = v;
         });
     __syncthreads();
   }
+}
+
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// the RB x 3 kernel values of output grid AL of half HALF at the thread's frequencies
+// (the kernel stride passes through an opaque move, so that the compiler
+// computes these 27 addresses here rather than all 162 of a tile up front)
+template <int HALF, int AL, int RB>
+__device__ __forceinline__ void load_kv(const float* __restrict__ spec, int otot, const int* off, float (&kv)[RB][3]) {
+  constexpr int K0 = kidx(HALF, AL, 0), K1 = kidx(HALF, AL, 1), K2 = kidx(HALF, AL, 2);
+  int ot;
+  asm volatile("mov.b32 %0, %1;" : "=r"(ot) : "r"(otot));
+  const float* s0 = spec + K0 * ot;
+  const float* s1 = spec + K1 * ot;
+  const float* s2 = spec + K2 * ot;
+#pragma unroll
+  for (int r = 0; r < RB; ++r) {
+    kv[r][0] = __ldg(s0 + off[r]);
+    kv[r][1] = __ldg(s1 + off[r]);
+    kv[r][2] = __ldg(s2 + off[r]);
+  }
+}
+
+// output grid AL of half HALF from the sign-scaled sources S: the sum over
+// the three sources, -i for the field blocks, s_a of the potential blocks
+// (s_y, or s_z inside the signed phase table phs), the output phase of z
+// grids, the first inverse stage (radix RB), and the store to the buffer
+template <int HALF, int AL, int RA, int RB, int TX, int LD>
+__device__ __forceinline__ void mac_store(const float (&kv)[RB][3], const C (&S)[3][RB], float sy, int j, int c,
+                                          const C* ph, const C* phs, C* buf) {
+  C o[RB];
+#pragma unroll
+  for (int r = 0; r < RB; ++r) {
+    C acc;
+    acc.x = fmaf(S[0][r].x, kv[r][0], fmaf(S[1][r].x, kv[r][1], S[2][r].x * kv[r][2]));
+    acc.y = fmaf(S[0][r].y, kv[r][0], fmaf(S[1][r].y, kv[r][1], S[2][r].y * kv[r][2]));
+    o[r] = HALF == 0 ? acc : cmul_mi(acc);
+    if (HALF == 0 && AL == 1) o[r] = cscale(o[r], sy);
+    if (AL == 2) o[r] = cmul(o[r], cconj(HALF == 0 ? phs[j + r * RA] : ph[j + r * RA]));
+  }
+  dft<RB, C>(o, true);
+#pragma unroll
+  for (int r = 0; r < RB; ++r) buf[(j * RB + r) * LD + AL * TX + c] = o[r];
+}
+
+template <int RA, int RB, int TX>
+__global__ void __launch_bounds__(RA * TX, 3) k_zpass_pipe(Geom g, C* __restrict__ data,
+                                                          const float* __restrict__ spec, int otot,
+                                                          const C* __restrict__ twf, int twn_f, int offB,
+                                                          const C* __restrict__ twv, int twn_v, int offA_tw,
+                                                          const C* __restrict__ phz, int nbatch, int nitems) {
+  constexpr int L = RA * RB, NT = RA * TX, LD = 3 * TX, LH = L / 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);      // [L][3][TX]: z lines between the stages
+  C* stg = buf + L * LD;                        // [3][L/2][TX]: the next tile's input planes
+  C* tf = stg + 3 * LH * TX;
+  C* tv = tf + twn_f;
+  C* ph = tv + twn_v;                           // e^{+i pi kz / Mz}
+  C* phs = ph + L;                              // s_z(kz) e^{+i pi kz / Mz}
+  int* colz = reinterpret_cast<int*>(phs + L);  // [2][TX] column offset in a z plane, by tile parity
+  int* coly = colz + 2 * TX;                    // [2][TX] its row ky
+  fast::load_table<NT>(tf, twf, twn_f);
+  fast::load_table<NT>(tv, twv, twn_v);
+  for (int i = threadIdx.x; i < L; i += NT) {
+    const C p = phz[i];
+    ph[i] = p;
+    phs[i] = i > L / 2 ? mk<C>(-p.x, -p.y) : p;
+  }
+  const int H = g.Hx, Lz = g.Lz;
+  const int64_t zstride = (int64_t)g.My * H;    // one z plane [My][H]
+  const int64_t gstride = (int64_t)Lz * zstride;
+  const int t = threadIdx.x, j = t / TX, c = t % TX;
+
+  // columns of tile `item` into colz/coly[par], and its input planes into
+  // the staging buffer (asynchronous; thread t copies column t % TX)
+  auto prefetch = [&](int item, int par) {
+    const int b = item % nbatch;
+    const int qq = (item / nbatch) * TX + c;    // < My H + TX < 2^31 (checked at launch)
+    const bool ok = qq < zstride;
+    const int i = qq / H, kx = qq - i * H;
+    const int ky = ok ? row_of(i, g.My) : 0;
+    const int col = ok ? ky * H + kx : 0;
+    if (t < TX) {
+      colz[par * TX + c] = col;
+      coly[par * TX + c] = ky;
+    }
+    if (ok) {
+      const C* src = data + (int64_t)b * 6 * gstride + col;
+#pragma unroll
+      for (int grid = 0; grid < 3; ++grid)
+        for (int z = j; z < Lz; z += NT / TX)
+          cp_async8(&stg[(grid * LH + z) * TX + c], src + grid * gstride + z * zstride);
+    }
+    cp_async_commit();
+  };
+
+  int par = 0;
+  if ((int)blockIdx.x < nitems) prefetch(blockIdx.x, 0);
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x, par ^= 1) {
+    const int b = item % nbatch;
+    const int ncol = min(TX, (int)(zstride - (int64_t)(item / nbatch) * TX));
+    C* base = data + (int64_t)b * 6 * gstride;
+    cp_async_wait_all();
+    __syncthreads();                            // staging and columns of this tile in; buffer free
+
+    // ---- stage A: forward radix RA (lower RA/2 inputs), staging -> buffer
+    fast::stage<L, RA, 1, LD, NT, false, RA / 2>(
+        tf,
+        [&](int line, int z) -> C {
+          const int grid = line / TX, cc = line % TX;
+          C v = mk<C>(0.f, 0.f);
+          if (cc < ncol && z < Lz) v = stg[(grid * LH + z) * TX + cc];
+          return v;
+        },
+        [&](int line, int pos, C v) { buf[pos * LD + line] = v; });
+    __syncthreads();                            // buffer complete, staging free
+    if (item + (int)gridDim.x < nitems) prefetch(item + gridDim.x, par ^ 1);
+
+    // ---- last forward stage (radix RB) into registers, sources scaled by s_b
+    const int ky = coly[par * TX + c];
+    const int kx = colz[par * TX + c] - ky * H;
+    const bool fy = ky > g.My / 2;
+    const float sy = fy ? -1.f : 1.f;
+    C S[3][RB];
+#pragma unroll
+    for (int be = 0; be < 3; ++be) {
+      C v[RB];
+#pragma unroll
+      for (int r = 0; r < RB; ++r) v[r] = buf[(j + r * RA) * LD + be * TX + c];
+      fast::twiddle<RB, false>(v, tf + offB, j);
+      dft<RB, C>(v, false);
+#pragma unroll
+      for (int r = 0; r < RB; ++r)
+        S[be][r] = be == 0 ? v[r] : be == 1 ? cscale(v[r], sy) : cmul(v[r], phs[j + r * RA]);
+    }
+    // kernel-octant offsets of the thread's frequencies (kz folded, ky folded, kx)
+    const int rec0 = (fy ? g.My - ky : ky) * H + kx;
+    const int zrec = g.Oy * H;
+    int off[RB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      const int kz = j + r * RA;
+      off[r] = (kz > L / 2 ? L - kz : kz) * zrec + rec0;
+    }
+    float ka[RB][3], kb[RB][3];
+    load_kv<0, 0, RB>(spec, otot, off, ka);
+    __syncthreads();                            // every stage-B input read: the buffer takes the outputs
+
+    // last inverse stage (radix RA with twiddles, outputs below Mz/2) of
+    // output grids 3 h .. 3 h + 2, buffer -> HBM, one butterfly at a time
+    // (the sources S stay live in registers meanwhile)
+    auto last_stage = [&](int h) {
+      constexpr int NB = L / RA, TOT = NB * LD;   // butterflies (j', line); NB = RB
+#pragma unroll 1
+      for (int item = t; item < TOT; item += NT) {
+        const int line = item % LD, jj = item / LD;
+        C v[RA];
+#pragma unroll
+        for (int r = 0; r < RA; ++r) v[r] = buf[(jj + r * NB) * LD + line];
+        fast::twiddle<RA, true>(v, tv + offA_tw, jj);
+        dft<RA, C>(v, true);
+        const int grid = line / TX + 3 * h, cc = line % TX;
+        if (cc < ncol) {
+          C* o = base + grid * gstride + colz[par * TX + cc] + jj * zstride;
+#pragma unroll
+          for (int r = 0; r < RA / 2; ++r)
+            if (jj + r * NB < Lz) o[(int64_t)r * NB * zstride] = v[r];
+        }
+      }
+    };
+    // ---- potential outputs; kernel values loaded one grid ahead
+    load_kv<0, 1, RB>(spec, otot, off, kb);
+    mac_store<0, 0, RA, RB, TX, LD>(ka, S, sy, j, c, ph, phs, buf);
+    load_kv<0, 2, RB>(spec, otot, off, ka);
+    mac_store<0, 1, RA, RB, TX, LD>(kb, S, sy, j, c, ph, phs, buf);
+    mac_store<0, 2, RA, RB, TX, LD>(ka, S, sy, j, c, ph, phs, buf);
+    __syncthreads();
+    last_stage(0);
+    __syncthreads();                            // the buffer takes the field outputs
+    // ---- field outputs
+    load_kv<1, 0, RB>(spec, otot, off, ka);
+    load_kv<1, 1, RB>(spec, otot, off, kb);
+    mac_store<1, 0, RA, RB, TX, LD>(ka, S, sy, j, c, ph, phs, buf);
+    load_kv<1, 2, RB>(spec, otot, off, ka);
+    mac_store<1, 1, RA, RB, TX, LD>(kb, S, sy, j, c, ph, phs, buf);
+    mac_store<1, 2, RA, RB, TX, LD>(ka, S, sy, j, c, ph, phs, buf);
+    __syncthreads();
+    last_stage(1);
+  }
+  cp_async_wait_all();
+}
+
+template <int RA, int RB, int TX>
+int launch_zpipe(const Handle& h, C* data, int B, cudaStream_t st) {
+  const Geom& g = h.g;
+  const Plan1D<float2>& pz = h.pzf[0];
+  const Plan1D<float2>& pv = h.pzfr[0];
+  constexpr int L = RA * RB, NT = RA * TX;
+  const size_t sm = ((size_t)L * 3 * TX + (size_t)3 * (L / 2) * TX + pz.twn + pv.twn + 2 * L) * sizeof(C) +
+                    4 * TX * sizeof(int);
+  const int64_t cols = (int64_t)g.My * g.Hx;
+  const int64_t items = (cols + TX - 1) / TX * B;
+  VC_CHECK(items < ((int64_t)1 << 31) && cols + TX < ((int64_t)1 << 31) &&
+               (int64_t)g.Hx * g.Oy * g.Oz * kNumKernels < ((int64_t)1 << 31),
+           VOXCAP_ERR_UNSUPPORTED, "grid too large for the compiled z pass");
+  VC_CHECK(2 * g.Lz <= L && g.My % 2 == 0, VOXCAP_ERR_UNSUPPORTED, "z padding shorter than twice the grid or odd My");
+  auto kern = k_zpass_pipe<RA, RB, TX>;
+  VC_TRY(set_smem(kern, sm));
+  int per_sm = 0, sms = 0;
+  VC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, sm));
+  VC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h.device));
+  VC_CHECK(per_sm > 0, VOXCAP_ERR_UNSUPPORTED, "the persistent z pass does not fit an SM");
+  const int grid = (int)std::min<int64_t>(items, (int64_t)per_sm * sms);
+  kern<<<grid, NT, sm, st>>>(g, data, h.spec_f.p, (int)((int64_t)g.Hx * g.Oy * g.Oz), pz.stw, pz.twn,
+                             pz.twoff[1], pv.stw, pv.twn, pv.twoff[1], h.phf[2], B, (int)items);
+  ::vc::note_launch();
+  VC_CUDA(cudaGetLastError());
+  return VOXCAP_OK;
 }
 
 template <int RA, int RB, int TX>
@@ -198,11 +455,14 @@ int launch_z(const Handle& h, C* data, int B, cudaStream_t st) {
   const Plan1D<float2>& pz = h.pzf[0];
   const Plan1D<float2>& pv = h.pzfr[0];
   constexpr int L = RA * RB;
-  const size_t sm = ((size_t)L * 3 * TX + (size_t)3 * RB * RA * TX + pz.twn + pv.twn + L) * sizeof(C);
+  const size_t sm = ((size_t)L * 3 * TX + (size_t)3 * RB * RA * TX + pz.twn + pv.twn + L) * sizeof(C) +
+                    2 * TX * sizeof(int);
   const int64_t cols = (int64_t)g.My * g.Hx;
   const int64_t tiles = (cols + TX - 1) / TX;
   VC_CHECK(tiles * B < ((int64_t)1 << 31) && (int64_t)g.Hx * g.Oy * g.Oz * kNumKernels < ((int64_t)1 << 31),
            VOXCAP_ERR_UNSUPPORTED, "grid too large for the compiled z pass");
+  VC_CHECK(2 * g.Lz <= L && g.My % 2 == 0 && cols + TX < ((int64_t)1 << 31), VOXCAP_ERR_UNSUPPORTED,
+           "z padding shorter than twice the grid, odd My or too many columns");
   auto kern = k_zpass_fast<RA, RB, TX>;
   VC_TRY(set_smem(kern, sm));
   kern<<<(unsigned)(tiles * B), RA * TX, sm, st>>>(g, data, h.spec_f.p, (int)((int64_t)g.Hx * g.Oy * g.Oz), pz.stw,
@@ -222,6 +482,7 @@ bool fast_z_ok(const Handle& h) {
 int fast_zpass(const Handle& h, float2* data, int B, cudaStream_t st) {
   const Plan1D<float2>& p = h.pzf[0];
   if (p.nst == 2 && p.radix[1] == 9) {
+    if (p.radix[0] == 16 && h.zfvar == 1) return launch_zpipe<16, 9, 8>(h, data, B, st);
     if (p.radix[0] == 16) return launch_z<16, 9, 16>(h, data, B, st);
     if (p.radix[0] == 8) return launch_z<8, 9, 16>(h, data, B, st);
     if (p.radix[0] == 4) return launch_z<4, 9, 16>(h, data, B, st);

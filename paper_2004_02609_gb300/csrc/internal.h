@@ -213,7 +213,8 @@ struct Handle {
   // FP32 product kernels: 0 generic passes, 1 compiled-plan passes where the
   // padded lengths have a compiled plan (fast_*.cu), -1 not chosen yet
   int path = -1;
-  int yvar = 0;                   // variant of the compiled y pass (tile width)
+  int yvar[2] = {0, 0};           // variants of the compiled forward / inverse y passes (tile width)
+  int zfvar = 0;                  // variant of the compiled z pass (0 one tile per CTA, 1 persistent)
   const double2* phd[3] = {nullptr, nullptr, nullptr};   // exp(+i pi k / M) per axis, k in [0, M)
   const float2* phf[3] = {nullptr, nullptr, nullptr};
   // Toeplitz tensors (FP64) and spectra

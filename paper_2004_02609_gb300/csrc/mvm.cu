@@ -330,7 +330,7 @@ int mvm(Handle& h, const T* x, T* y, int nrhs, bool adjoint, T* field_out, void*
   const int ybufs = plan_of<T>(h, 1).nst >= 3 ? 2 : 1;
   if (fast_y) {
     VC_TRY(fast_ypass(h, false, GI, reinterpret_cast<const float2*>(bufX), reinterpret_cast<float2*>(bufY),
-                      (int64_t)GI * gX, (int64_t)6 * gY, B, h.yvar, st));
+                      (int64_t)GI * gX, (int64_t)6 * gY, B, h.yvar[0], st));
   } else {
     const int TXy = TXf;
     const int TBy = TXy >= 16 ? 256 : 128;
@@ -352,7 +352,7 @@ int mvm(Handle& h, const T* x, T* y, int nrhs, bool adjoint, T* field_out, void*
   // yinv: bufY [B][6] (first GO grids) -> bufX [B][GO]
   if (fast_y) {
     VC_TRY(fast_ypass(h, true, GO, reinterpret_cast<const float2*>(bufY), reinterpret_cast<float2*>(bufX),
-                      (int64_t)6 * gY, (int64_t)GO * gX, B, h.yvar, st));
+                      (int64_t)6 * gY, (int64_t)GO * gX, B, h.yvar[1], st));
   } else {
     const int TXy = TXi;
     const int TBy = TXy >= 16 ? 256 : 128;

@@ -431,7 +431,7 @@ static int gmres(Handle& h, const T* r, T* d, int nrhs, const double* rtol_host,
   // ---- the restart-cycle graph, built once per key ----
   const uintptr_t key[10] = {sizeof(T), (uintptr_t)adjoint, (uintptr_t)nrhs, (uintptr_t)N, (uintptr_t)m,
                              (uintptr_t)h.solver_ws.p, (uintptr_t)h.ws.p,
-                             (uintptr_t)(h.path + 2) | ((uintptr_t)h.yvar << 8) | ((uintptr_t)h.zvar << 16) |
+                             (uintptr_t)(h.path + 2) | ((uintptr_t)(h.yvar[0] + 2 * h.yvar[1] + 4 * h.zfvar) << 8) | ((uintptr_t)h.zvar << 16) |
                                  ((uintptr_t)(h.ztx + 2) << 24),
                              (uintptr_t)(h.ytx[0] + 2) | ((uintptr_t)(h.ytx[1] + 2) << 8), (uintptr_t)h.act_map.d};
   bool same = h.gm.exec != nullptr;

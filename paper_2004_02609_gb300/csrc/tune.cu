@@ -17,7 +17,7 @@ namespace vc {
 
 namespace {
 std::mutex g_tune_mu;
-std::map<std::array<int, 8>, std::array<int, 6>> g_tune;
+std::map<std::array<int, 8>, std::array<int, 8>> g_tune;
 }  // namespace
 
 static int tune(Handle& h, bool use_cache) {
@@ -35,7 +35,9 @@ static int tune(Handle& h, bool use_cache) {
       h.ytx[0] = it->second[2];
       h.ytx[1] = it->second[3];
       h.path = it->second[4];
-      h.yvar = it->second[5];
+      h.yvar[0] = it->second[5];
+      h.yvar[1] = it->second[6];
+      h.zfvar = it->second[7];
       return VOXCAP_OK;
     }
   }
@@ -67,7 +69,8 @@ static int tune(Handle& h, bool use_cache) {
   };
   h.ytx[0] = h.ytx[1] = -1;
   h.path = 0;
-  h.yvar = 0;
+  h.yvar[0] = h.yvar[1] = 0;
+  h.zfvar = 0;
   float best_ms = 1e30f;
   int best_v = 0, best_tx = -1;
   for (int v = 0; v < h.nzvar; ++v)
@@ -102,24 +105,31 @@ static int tune(Handle& h, bool use_cache) {
   // then the compiled-plan passes, where the lengths have a plan (two tile
   // widths for the longest y plan)
   if (fast_plan_ok(h.pf[1]) || fast_z_ok(h) || fast_x_ok(h)) {
+    // the compiled passes with their default variants, then each variant
+    // switch kept where it is faster (the persistent z pass; the narrower
+    // tiles of the forward and of the inverse y pass on the longest plan)
     const bool two = h.pf[1].nst == 3 && h.pf[1].radix[0] == 16 && h.pf[1].radix[1] == 8;
-    int best_path = 0, best_var = 0;
-    for (int v = 0; v < (two ? 2 : 1); ++v) {
-      h.path = 1;
-      h.yvar = v;
-      float ms;
-      VC_TRY(time_products(&ms));
-      if (ms >= 0.0f && ms < best_ms) {
-        best_ms = ms;
-        best_path = 1;
-        best_var = v;
+    const bool zpipe = fast_z_ok(h) && h.pzf[0].radix[0] == 16;
+    h.path = 1;
+    float ms;
+    VC_TRY(time_products(&ms));
+    if (ms >= 0.0f && ms < best_ms) {
+      best_ms = ms;
+      int* sw[3] = {&h.zfvar, &h.yvar[0], &h.yvar[1]};
+      const bool avail[3] = {zpipe, two, two};
+      for (int k = 0; k < 3; ++k) {
+        if (!avail[k]) continue;
+        *sw[k] = 1;
+        VC_TRY(time_products(&ms));
+        if (ms >= 0.0f && ms < best_ms) best_ms = ms;
+        else *sw[k] = 0;
       }
+    } else {
+      h.path = 0;
     }
-    h.path = best_path;
-    h.yvar = best_var;
   }
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tune[key] = {h.zvar, h.ztx, h.ytx[0], h.ytx[1], h.path, h.yvar};
+  g_tune[key] = {h.zvar, h.ztx, h.ytx[0], h.ytx[1], h.path, h.yvar[0], h.yvar[1], h.zfvar};
   return VOXCAP_OK;
 }
 
