@@ -411,9 +411,10 @@ int voxcap_setup_times(const voxcap_t* h, double* seconds);
  *           72, 144; forward z pass only), the generic passes elsewhere, each
  *           in its default launch variant;
  *  path 1 + variant bits: 2 = the persistent z pass with asynchronous
- *           prefetch of the next tile (z length 144), 4 / 8 = the narrower
- *           tiles of the forward / inverse y pass (y length 1152); a bit
- *           that does not apply to the handle's lengths changes nothing.
+ *           prefetch of the next tile (z length 144), 4 / 8 = the persistent
+ *           forward / inverse y pass, double-buffered with asynchronous
+ *           prefetch (compiled y lengths); a bit that does not apply to the
+ *           handle's lengths changes nothing.
  *           The variants of path 1 differ in tiling only: every line is
  *           transformed with the same arithmetic, so they give the same bits;
  *  path -1  re-run the set-up autotuner, which times the generic variants,

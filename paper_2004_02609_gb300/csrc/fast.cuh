@@ -76,8 +76,9 @@ __device__ __forceinline__ void stage(const C* __restrict__ tw, Ld ld, St st) {
 // The same stage in place on buf (element (pos, c) at pos * PT + c, pitch
 // PT >= TX): all inputs of a thread's butterflies are read, the block
 // synchronises, the outputs are written, and the block synchronises again.
-template <int L, int R, int NS, int TX, int NT, bool INV, int PT = TX, int RIN = R, int ROUT = R>
-__device__ __forceinline__ void stage_inplace(C* buf, const C* __restrict__ tw) {
+// ld(c, pos) reads the input (default: buf itself).
+template <int L, int R, int NS, int TX, int NT, bool INV, int PT = TX, int RIN = R, int ROUT = R, typename Ld>
+__device__ __forceinline__ void stage_inplace_ld(C* buf, const C* __restrict__ tw, Ld ld) {
   constexpr int NB = L / R, TOT = NB * TX, IT = (TOT + NT - 1) / NT;
   static_assert(RIN == R || (RIN * 2 == R && NS == 1), "half inputs in a first stage only");
   C v[IT][R];
@@ -87,7 +88,7 @@ __device__ __forceinline__ void stage_inplace(C* buf, const C* __restrict__ tw) 
     if (TOT % NT == 0 || item < TOT) {
       const int c = item % TX, j = item / TX;
 #pragma unroll
-      for (int r = 0; r < RIN; ++r) v[it][r] = buf[(j + r * NB) * PT + c];
+      for (int r = 0; r < RIN; ++r) v[it][r] = ld(c, j + r * NB);
     }
   }
   __syncthreads();
@@ -105,6 +106,22 @@ __device__ __forceinline__ void stage_inplace(C* buf, const C* __restrict__ tw) 
   }
   __syncthreads();
 }
+
+template <int L, int R, int NS, int TX, int NT, bool INV, int PT = TX, int RIN = R, int ROUT = R>
+__device__ __forceinline__ void stage_inplace(C* buf, const C* __restrict__ tw) {
+  stage_inplace_ld<L, R, NS, TX, NT, INV, PT, RIN, ROUT>(buf, tw,
+                                                         [&](int c, int pos) -> C { return buf[pos * PT + c]; });
+}
+
+// cp.async of 8 bytes global -> shared (cached in L1 and L2), its group
+// commit, and the wait for all of this thread's groups
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // A whole transform of TX interleaved lines held in buf, every stage in
 // place (twiddle tables of the plan's stages at tw + off[s]).  HIN: the

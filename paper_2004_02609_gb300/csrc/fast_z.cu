@@ -19,9 +19,11 @@
 // planes z <= N_z to HBM (only the outputs below Mz/2 are computed).
 //
 // k_zpass_pipe (Mz = 16 * 9, TX = 8) is the persistent form of the same
-// pass: a CTA loops over tiles, and while it works on one tile the next
-// tile's input planes arrive in a staging buffer by cp.async, so that
-// stage A reads shared memory instead of waiting on HBM.  Each thread keeps
+// pass: a CTA takes tiles from a device counter (in order, so that the tiles
+// in flight stay close together and the mirrored rows still share the
+// spectra in L2), and while it works on one tile the next tile's input
+// planes arrive in a staging buffer by cp.async, so that stage A reads
+// shared memory instead of waiting on HBM.  Each thread keeps
 // its 27 charge spectra in registers (no second buffer: three CTAs fit an
 // SM), loads the kernel values of the next output grid while it computes
 // the current one, and folds the fold signs of Eq. 12's real spectra into
@@ -225,13 +227,9 @@ __global__ void __launch_bounds__(RA * TX, 2) k_zpass_fast(Geom g, C* __restrict
   }
 }
 
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
-               "l"(gmem)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+using fast::cp_async8;
+using fast::cp_async_commit;
+using fast::cp_async_wait_all;
 
 // the RB x 3 kernel values of output grid AL of half HALF at the thread's frequencies
 // (the kernel stride passes through an opaque move, so that the compiler
@@ -279,8 +277,10 @@ __global__ void __launch_bounds__(RA * TX, 3) k_zpass_pipe(Geom g, C* __restrict
                                                           const float* __restrict__ spec, int otot,
                                                           const C* __restrict__ twf, int twn_f, int offB,
                                                           const C* __restrict__ twv, int twn_v, int offA_tw,
-                                                          const C* __restrict__ phz, int nbatch, int nitems) {
+                                                          const C* __restrict__ phz, int nbatch, int nitems,
+                                                          int* __restrict__ queue) {
   constexpr int L = RA * RB, NT = RA * TX, LD = 3 * TX, LH = L / 2;
+  __shared__ int s_item[2];                     // tiles taken from the counter, by parity
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);      // [L][3][TX]: z lines between the stages
   C* stg = buf + L * LD;                        // [3][L/2][TX]: the next tile's input planes
@@ -326,8 +326,14 @@ __global__ void __launch_bounds__(RA * TX, 3) k_zpass_pipe(Geom g, C* __restrict
   };
 
   int par = 0;
-  if ((int)blockIdx.x < nitems) prefetch(blockIdx.x, 0);
-  for (int item = blockIdx.x; item < nitems; item += gridDim.x, par ^= 1) {
+  if (t == 0) s_item[0] = atomicAdd(queue, 1);
+  __syncthreads();
+  int item = s_item[0];
+  if (item < nitems) prefetch(item, 0);
+  while (item < nitems) {
+    // the tile after this one (read by all threads after the barriers below;
+    // the slot was last read in the previous tile)
+    if (t == 0) s_item[par ^ 1] = atomicAdd(queue, 1);
     const int b = item % nbatch;
     const int ncol = min(TX, (int)(zstride - (int64_t)(item / nbatch) * TX));
     C* base = data + (int64_t)b * 6 * gstride;
@@ -345,7 +351,8 @@ __global__ void __launch_bounds__(RA * TX, 3) k_zpass_pipe(Geom g, C* __restrict
         },
         [&](int line, int pos, C v) { buf[pos * LD + line] = v; });
     __syncthreads();                            // buffer complete, staging free
-    if (item + (int)gridDim.x < nitems) prefetch(item + gridDim.x, par ^ 1);
+    const int next = s_item[par ^ 1];
+    if (next < nitems) prefetch(next, par ^ 1);
 
     // ---- last forward stage (radix RB) into registers, sources scaled by s_b
     const int ky = coly[par * TX + c];
@@ -417,6 +424,8 @@ __global__ void __launch_bounds__(RA * TX, 3) k_zpass_pipe(Geom g, C* __restrict
     mac_store<1, 2, RA, RB, TX, LD>(ka, S, sy, j, c, ph, phs, buf);
     __syncthreads();
     last_stage(1);
+    item = next;
+    par ^= 1;
   }
   cp_async_wait_all();
 }
@@ -442,8 +451,10 @@ int launch_zpipe(const Handle& h, C* data, int B, cudaStream_t st) {
   VC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h.device));
   VC_CHECK(per_sm > 0, VOXCAP_ERR_UNSUPPORTED, "the persistent z pass does not fit an SM");
   const int grid = (int)std::min<int64_t>(items, (int64_t)per_sm * sms);
+  VC_CHECK(h.zqueue.p != nullptr, VOXCAP_ERR_UNSUPPORTED, "tile counter of the persistent z pass missing");
+  VC_CUDA(cudaMemsetAsync(h.zqueue.p, 0, sizeof(int), st));
   kern<<<grid, NT, sm, st>>>(g, data, h.spec_f.p, (int)((int64_t)g.Hx * g.Oy * g.Oz), pz.stw, pz.twn,
-                             pz.twoff[1], pv.stw, pv.twn, pv.twoff[1], h.phf[2], B, (int)items);
+                             pz.twoff[1], pv.stw, pv.twn, pv.twoff[1], h.phf[2], B, (int)items, h.zqueue.p);
   ::vc::note_launch();
   VC_CUDA(cudaGetLastError());
   return VOXCAP_OK;

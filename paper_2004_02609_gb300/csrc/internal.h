@@ -215,6 +215,7 @@ struct Handle {
   int path = -1;
   int yvar[2] = {0, 0};           // variants of the compiled forward / inverse y passes (tile width)
   int zfvar = 0;                  // variant of the compiled z pass (0 one tile per CTA, 1 persistent)
+  DBuf<int> zqueue;               // tile counter of the persistent z pass (allocated at set-up)
   const double2* phd[3] = {nullptr, nullptr, nullptr};   // exp(+i pi k / M) per axis, k in [0, M)
   const float2* phf[3] = {nullptr, nullptr, nullptr};
   // Toeplitz tensors (FP64) and spectra

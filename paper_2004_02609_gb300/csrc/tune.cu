@@ -23,6 +23,7 @@ std::map<std::array<int, 8>, std::array<int, 8>> g_tune;
 static int tune(Handle& h, bool use_cache) {
   const int64_t N = h.pan.N;
   if (N == 0) return VOXCAP_OK;
+  VC_TRY(h.zqueue.alloc(1));       // before any product: none may allocate inside a captured graph
   const int nrhs = std::max(1, h.pan.m_max);
   const Geom& g = h.g;
   const std::array<int, 8> key = {h.device, g.Mx, g.My, g.Mz, g.nx, g.ny, g.nz, h.pan.S * nrhs};
@@ -106,9 +107,9 @@ static int tune(Handle& h, bool use_cache) {
   // widths for the longest y plan)
   if (fast_plan_ok(h.pf[1]) || fast_z_ok(h) || fast_x_ok(h)) {
     // the compiled passes with their default variants, then each variant
-    // switch kept where it is faster (the persistent z pass; the narrower
-    // tiles of the forward and of the inverse y pass on the longest plan)
-    const bool two = h.pf[1].nst == 3 && h.pf[1].radix[0] == 16 && h.pf[1].radix[1] == 8;
+    // switch kept where it is faster (the persistent z pass, the persistent
+    // forward and inverse y passes)
+    const bool ypipe = fast_plan_ok(h.pf[1]);
     const bool zpipe = fast_z_ok(h) && h.pzf[0].radix[0] == 16;
     h.path = 1;
     float ms;
@@ -116,7 +117,7 @@ static int tune(Handle& h, bool use_cache) {
     if (ms >= 0.0f && ms < best_ms) {
       best_ms = ms;
       int* sw[3] = {&h.zfvar, &h.yvar[0], &h.yvar[1]};
-      const bool avail[3] = {zpipe, two, two};
+      const bool avail[3] = {zpipe, ypipe, ypipe};
       for (int k = 0; k < 3; ++k) {
         if (!avail[k]) continue;
         *sw[k] = 1;

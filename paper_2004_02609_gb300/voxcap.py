@@ -226,7 +226,7 @@ class VoxCap:
     def set_product_path(self, path=-1):
         """FP32 product kernels: 0 generic, 1 compiled radix plans where the
         padded lengths have one (plus variant bits 2: persistent z pass, 4 /
-        8: narrow forward / inverse y tiles), -1 re-tune, -2 query; returns
+        8: persistent forward / inverse y pass), -1 re-tune, -2 query; returns
         the path in force with its variant bits."""
         out = ctypes.c_int()
         _check(lib().voxcap_set_product_path(self._h, int(path), ctypes.byref(out)))
