@@ -4,10 +4,13 @@
 // 9 normal-field blocks; Eq. 12 folds the other three potential blocks) and
 // the inverse z transforms back to the N_z+1 planes the panels need.
 //
-// A CTA (RA * TX threads) takes TX consecutive (ky, kx) columns of one batch
-// item, the rows ky taken in the order 0, 1, My-1, 2, My-2, ... so that the
-// two rows that share a folded row of the kernel spectra (ky and My-ky) run
-// back to back and the second reads the spectra from L2.  Stage A (radix RA,
+// A CTA (RA * TX threads) takes TX consecutive kx columns of one row ky of
+// one batch item, the rows taken in the order 0, 1, My-1, 2, My-2, ... so
+// that the two rows that share a folded row of the kernel spectra (ky and
+// My-ky) run back to back and the second reads the spectra from L2.  The
+// FP32 spectra are read in their blocked layout [Oy][Hx/8][Oz][15][8]: the
+// spectra of a tile are one or two contiguous blocks of 35 KB (Mz = 144), not
+// 1095 rows scattered over the whole octant array.  Stage A (radix RA,
 // only its lower RA/2 inputs: planes z >= Mz/2 are padding) reads the N_z+1
 // non-zero planes of the three input grids from HBM and fills the shared
 // buffer [Mz][3][TX]; each thread
@@ -71,16 +74,16 @@ constexpr int kidx(int half, int al, int be) {
 // the sum over the 3 source grids, the output half-voxel phase of z grids,
 // the first inverse stage, and the store to the line buffer.
 template <int HALF, int AL, int RA, int RB, int NT, int TX, int LD>
-__device__ __forceinline__ void mac_out(const float* __restrict__ spec, int otot, const int* off, bool col_ok,
-                                        float sy, const C* S, int t, int j, int c, const C* ph, C* buf) {
+__device__ __forceinline__ void mac_out(const float* __restrict__ spec, const int* off, float sy, const C* S,
+                                        int t, int j, int c, const C* ph, C* buf) {
   constexpr int L = RA * RB;
   constexpr int K0 = kidx(HALF, AL, 0), K1 = kidx(HALF, AL, 1), K2 = kidx(HALF, AL, 2);
   float kv[RB][3];
 #pragma unroll
   for (int r = 0; r < RB; ++r) {
-    kv[r][0] = col_ok ? __ldg(spec + K0 * otot + off[r]) : 0.f;
-    kv[r][1] = col_ok ? __ldg(spec + K1 * otot + off[r]) : 0.f;
-    kv[r][2] = col_ok ? __ldg(spec + K2 * otot + off[r]) : 0.f;
+    kv[r][0] = __ldg(spec + off[r] + K0 * kSpecBlk);
+    kv[r][1] = __ldg(spec + off[r] + K1 * kSpecBlk);
+    kv[r][2] = __ldg(spec + off[r] + K2 * kSpecBlk);
   }
   C o[RB];
 #pragma unroll
@@ -107,9 +110,15 @@ __device__ __forceinline__ int row_of(int i, int My) {
   return (i & 1) || i == 0 ? p : My - p;
 }
 
+// offset of column kxa's spectra block entry (kz folded, ky folded) in the
+// blocked spectra, without the kernel's K * kSpecBlk
+__device__ __forceinline__ int spec_block(const Geom& g, int nm, int kyf, int kxa) {
+  return ((kyf * nm + kxa / kSpecBlk) * g.Oz) * (kNumKernels * kSpecBlk) + kxa % kSpecBlk;
+}
+
 template <int RA, int RB, int TX>
 __global__ void __launch_bounds__(RA * TX, 2) k_zpass_fast(Geom g, C* __restrict__ data,
-                                                          const float* __restrict__ spec, int otot,
+                                                          const float* __restrict__ spec, int nm,
                                                           const C* __restrict__ twf, int twn_f, int offB,
                                                           const C* __restrict__ twv, int twn_v, int offA_tw,
                                                           const C* __restrict__ phz, int nbatch) {
@@ -122,26 +131,21 @@ __global__ void __launch_bounds__(RA * TX, 2) k_zpass_fast(Geom g, C* __restrict
   C* tf = S + 3 * RB * NT;
   C* tv = tf + twn_f;
   C* ph = tv + twn_v;
-  int* colz = reinterpret_cast<int*>(ph + L);   // [TX] column offset in a z plane (ky H + kx)
-  int* coly = colz + TX;                        // [TX] its row ky
   fast::load_table<NT>(tf, twf, twn_f);
   fast::load_table<NT>(tv, twv, twn_v);
   fast::load_table<NT>(ph, phz, L);
   const int H = g.Hx;
   const int b = blockIdx.x % nbatch;                      // batch items of a tile run together
   const int64_t zstride = (int64_t)g.My * H;              // one z plane [My][H]
-  // first column of the tile in the processing order (rows by row_of)
-  const int64_t q0 = (int64_t)(blockIdx.x / nbatch) * TX;
   const int64_t gstride = (int64_t)g.Lz * zstride;
-  C* base = data + (int64_t)b * 6 * gstride;
-  const int ncol = (int)min((int64_t)TX, zstride - q0);
-  if (threadIdx.x < TX) {
-    const int qq = (int)q0 + (int)threadIdx.x;                // < My H < 2^31 (checked at launch)
-    const int i = qq / H, kx = qq - i * H;
-    const int ky = threadIdx.x < ncol ? row_of(i, g.My) : 0;
-    coly[threadIdx.x] = ky;
-    colz[threadIdx.x] = threadIdx.x < ncol ? ky * H + kx : 0;
-  }
+  // the tile: row i of the processing order, columns kx0 .. kx0 + ncol - 1
+  const int ntr = (H + TX - 1) / TX;
+  const int tile = blockIdx.x / nbatch, i = tile / ntr;
+  const int kx0 = (tile - i * ntr) * TX;
+  const int ky = row_of(i, g.My);
+  const int ncol = min(TX, H - kx0);
+  const int col0 = ky * H + kx0;                          // < My H < 2^31 (checked at launch)
+  C* base = data + (int64_t)b * 6 * gstride + col0;
   const int Lz = g.Lz;
   __syncthreads();
 
@@ -151,7 +155,7 @@ __global__ void __launch_bounds__(RA * TX, 2) k_zpass_fast(Geom g, C* __restrict
       [&](int line, int z) -> C {
         const int grid = line / TX, c = line % TX;
         C v = mk<C>(0.f, 0.f);
-        if (c < ncol && z < Lz) v = base[grid * gstride + z * zstride + colz[c]];
+        if (c < ncol && z < Lz) v = base[grid * gstride + z * zstride + c];
         return v;
       },
       [&](int line, int pos, C v) { buf[pos * LD + line] = v; });
@@ -160,7 +164,6 @@ __global__ void __launch_bounds__(RA * TX, 2) k_zpass_fast(Geom g, C* __restrict
   // ---- last forward stage (radix RB): thread (j, c) gets kz = j + RA r
   const int t = threadIdx.x;
   const int j = t / TX, c = t % TX;
-  const bool col_ok = c < ncol;
 #pragma unroll
   for (int be = 0; be < 3; ++be) {
     C v[RB];
@@ -176,19 +179,17 @@ __global__ void __launch_bounds__(RA * TX, 2) k_zpass_fast(Geom g, C* __restrict
   }
   __syncthreads();                                      // the buffer takes the outputs now
 
-  // spectral index of the column's frequencies (kz folded, ky folded, kx)
-  // in a kernel's octant [Oz][Oy][Hx]; 32-bit (the launch checks the size)
-  const int ky = coly[c];
-  const int kx = colz[c] - ky * H;
+  // the column's frequencies (kz folded, ky folded, kx) in the blocked
+  // spectra; 32-bit (the launch checks the size); a column past the row's
+  // end reads column kx0's values, computed and never stored
   const bool fy = ky > g.My / 2;
   const float sy = fy ? -1.f : 1.f;
-  const int rec0 = (fy ? g.My - ky : ky) * H + kx;
-  const int zrec = g.Oy * H;
+  const int sb = spec_block(g, nm, fy ? g.My - ky : ky, kx0 + (c < ncol ? c : 0));
   int off[RB];
 #pragma unroll
   for (int r = 0; r < RB; ++r) {
     const int kz = j + r * RA;
-    off[r] = (kz > L / 2 ? L - kz : kz) * zrec + rec0;
+    off[r] = (kz > L / 2 ? L - kz : kz) * (kNumKernels * kSpecBlk) + sb;
   }
 
 #pragma unroll 1
@@ -196,24 +197,23 @@ __global__ void __launch_bounds__(RA * TX, 2) k_zpass_fast(Geom g, C* __restrict
     // potential outputs (half 0: kernels 0..5, Eq. 12 pairs shared) or
     // normal-field outputs (half 1: kernels 6..14, times -i), one output
     // grid at a time; the 3 RB kernel values of a grid are loaded together
-    // (the kernel stride passes through an opaque move and the empty asm
-    // statements separate the grids, so that the compiler neither hoists
-    // the 162 load addresses out of this loop nor one grid's loads into the
-    // previous grid's work: both would only cost registers)
-    int ot;
-    asm volatile("mov.b32 %0, %1;" : "=r"(ot) : "r"(otot));
+    // (the spectra pointer passes through an opaque move per grid, so that
+    // the compiler hoists no grid's loads into the previous grid's work,
+    // which would only cost registers)
+    const float* sp;
+    asm volatile("mov.b64 %0, %1;" : "=l"(sp) : "l"(spec));
     if (half == 0) {
-      mac_out<0, 0, RA, RB, NT, TX, LD>(spec, ot, off, col_ok, sy, S, t, j, c, ph, buf);
-      asm volatile("" ::: "memory");
-      mac_out<0, 1, RA, RB, NT, TX, LD>(spec, ot, off, col_ok, sy, S, t, j, c, ph, buf);
-      asm volatile("" ::: "memory");
-      mac_out<0, 2, RA, RB, NT, TX, LD>(spec, ot, off, col_ok, sy, S, t, j, c, ph, buf);
+      mac_out<0, 0, RA, RB, NT, TX, LD>(sp, off, sy, S, t, j, c, ph, buf);
+      asm volatile("mov.b64 %0, %1;" : "=l"(sp) : "l"(spec));
+      mac_out<0, 1, RA, RB, NT, TX, LD>(sp, off, sy, S, t, j, c, ph, buf);
+      asm volatile("mov.b64 %0, %1;" : "=l"(sp) : "l"(spec));
+      mac_out<0, 2, RA, RB, NT, TX, LD>(sp, off, sy, S, t, j, c, ph, buf);
     } else {
-      mac_out<1, 0, RA, RB, NT, TX, LD>(spec, ot, off, col_ok, sy, S, t, j, c, ph, buf);
-      asm volatile("" ::: "memory");
-      mac_out<1, 1, RA, RB, NT, TX, LD>(spec, ot, off, col_ok, sy, S, t, j, c, ph, buf);
-      asm volatile("" ::: "memory");
-      mac_out<1, 2, RA, RB, NT, TX, LD>(spec, ot, off, col_ok, sy, S, t, j, c, ph, buf);
+      mac_out<1, 0, RA, RB, NT, TX, LD>(sp, off, sy, S, t, j, c, ph, buf);
+      asm volatile("mov.b64 %0, %1;" : "=l"(sp) : "l"(spec));
+      mac_out<1, 1, RA, RB, NT, TX, LD>(sp, off, sy, S, t, j, c, ph, buf);
+      asm volatile("mov.b64 %0, %1;" : "=l"(sp) : "l"(spec));
+      mac_out<1, 2, RA, RB, NT, TX, LD>(sp, off, sy, S, t, j, c, ph, buf);
     }
     __syncthreads();
     // ---- last inverse stage (radix RA), buffer -> HBM, planes z < Lz
@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(RA * TX, 2) k_zpass_fast(Geom g, C* __restrict
         tv + offA_tw, [&](int line, int pos) -> C { return buf[pos * LD + line]; },
         [&](int line, int z, C v) {
           const int grid = line / TX + 3 * half, cc = line % TX;
-          if (cc < ncol && z < Lz) base[grid * gstride + z * zstride + colz[cc]] = v;
+          if (cc < ncol && z < Lz) base[grid * gstride + z * zstride + cc] = v;
         });
     __syncthreads();
   }
@@ -232,21 +232,18 @@ using fast::cp_async_commit;
 using fast::cp_async_wait_all;
 
 // the RB x 3 kernel values of output grid AL of half HALF at the thread's frequencies
-// (the kernel stride passes through an opaque move, so that the compiler
-// computes these 27 addresses here rather than all 162 of a tile up front)
+// (the spectra pointer passes through an opaque move, so that the
+// compiler issues these 27 loads here rather than all 162 of a tile up front)
 template <int HALF, int AL, int RB>
-__device__ __forceinline__ void load_kv(const float* __restrict__ spec, int otot, const int* off, float (&kv)[RB][3]) {
+__device__ __forceinline__ void load_kv(const float* __restrict__ spec, const int* off, float (&kv)[RB][3]) {
   constexpr int K0 = kidx(HALF, AL, 0), K1 = kidx(HALF, AL, 1), K2 = kidx(HALF, AL, 2);
-  int ot;
-  asm volatile("mov.b32 %0, %1;" : "=r"(ot) : "r"(otot));
-  const float* s0 = spec + K0 * ot;
-  const float* s1 = spec + K1 * ot;
-  const float* s2 = spec + K2 * ot;
+  const float* sp;
+  asm volatile("mov.b64 %0, %1;" : "=l"(sp) : "l"(spec));
 #pragma unroll
   for (int r = 0; r < RB; ++r) {
-    kv[r][0] = __ldg(s0 + off[r]);
-    kv[r][1] = __ldg(s1 + off[r]);
-    kv[r][2] = __ldg(s2 + off[r]);
+    kv[r][0] = __ldg(sp + off[r] + K0 * kSpecBlk);
+    kv[r][1] = __ldg(sp + off[r] + K1 * kSpecBlk);
+    kv[r][2] = __ldg(sp + off[r] + K2 * kSpecBlk);
   }
 }
 
@@ -272,9 +269,33 @@ __device__ __forceinline__ void mac_store(const float (&kv)[RB][3], const C (&S)
   for (int r = 0; r < RB; ++r) buf[(j * RB + r) * LD + AL * TX + c] = o[r];
 }
 
+// the 6 distinct potential kernels (0..5) at the thread's frequencies
+template <int RB>
+__device__ __forceinline__ void load_pot(const float* __restrict__ spec, const int* off, float (&kp)[6][RB]) {
+#pragma unroll
+  for (int k = 0; k < 6; ++k)
+#pragma unroll
+    for (int r = 0; r < RB; ++r) kp[k][r] = __ldg(spec + off[r] + k * kSpecBlk);
+}
+
+// potential output grid AL from the 6 loaded potential kernels
+template <int AL, int RA, int RB, int TX, int LD>
+__device__ __forceinline__ void mac_store_pot(const float (&kp)[6][RB], const C (&S)[3][RB], float sy, int j, int c,
+                                              const C* ph, const C* phs, C* buf) {
+  constexpr int K0 = kidx(0, AL, 0), K1 = kidx(0, AL, 1), K2 = kidx(0, AL, 2);
+  float kv[RB][3];
+#pragma unroll
+  for (int r = 0; r < RB; ++r) {
+    kv[r][0] = kp[K0][r];
+    kv[r][1] = kp[K1][r];
+    kv[r][2] = kp[K2][r];
+  }
+  mac_store<0, AL, RA, RB, TX, LD>(kv, S, sy, j, c, ph, phs, buf);
+}
+
 template <int RA, int RB, int TX>
 __global__ void __launch_bounds__(RA * TX, 3) k_zpass_pipe(Geom g, C* __restrict__ data,
-                                                          const float* __restrict__ spec, int otot,
+                                                          const float* __restrict__ spec, int nm,
                                                           const C* __restrict__ twf, int twn_f, int offB,
                                                           const C* __restrict__ twv, int twn_v, int offA_tw,
                                                           const C* __restrict__ phz, int nbatch, int nitems,
@@ -288,8 +309,6 @@ __global__ void __launch_bounds__(RA * TX, 3) k_zpass_pipe(Geom g, C* __restrict
   C* tv = tf + twn_f;
   C* ph = tv + twn_v;                           // e^{+i pi kz / Mz}
   C* phs = ph + L;                              // s_z(kz) e^{+i pi kz / Mz}
-  int* colz = reinterpret_cast<int*>(phs + L);  // [2][TX] column offset in a z plane, by tile parity
-  int* coly = colz + 2 * TX;                    // [2][TX] its row ky
   fast::load_table<NT>(tf, twf, twn_f);
   fast::load_table<NT>(tv, twv, twn_v);
   for (int i = threadIdx.x; i < L; i += NT) {
@@ -301,22 +320,28 @@ __global__ void __launch_bounds__(RA * TX, 3) k_zpass_pipe(Geom g, C* __restrict
   const int64_t zstride = (int64_t)g.My * H;    // one z plane [My][H]
   const int64_t gstride = (int64_t)Lz * zstride;
   const int t = threadIdx.x, j = t / TX, c = t % TX;
-
-  // columns of tile `item` into colz/coly[par], and its input planes into
-  // the staging buffer (asynchronous; thread t copies column t % TX)
-  auto prefetch = [&](int item, int par) {
-    const int b = item % nbatch;
-    const int qq = (item / nbatch) * TX + c;    // < My H + TX < 2^31 (checked at launch)
-    const bool ok = qq < zstride;
-    const int i = qq / H, kx = qq - i * H;
-    const int ky = ok ? row_of(i, g.My) : 0;
-    const int col = ok ? ky * H + kx : 0;
-    if (t < TX) {
-      colz[par * TX + c] = col;
-      coly[par * TX + c] = ky;
-    }
-    if (ok) {
-      const C* src = data + (int64_t)b * 6 * gstride + col;
+  const int ntr = (H + TX - 1) / TX;            // tiles per row
+  // tile `item`: batch item b, row ky (row i of the processing order),
+  // columns kx0 .. kx0 + ncol - 1 starting at col0 = ky H + kx0 of a plane
+  struct Tile {
+    int b, ky, kx0, ncol, col0;
+  };
+  auto tile_of = [&](int item) {
+    Tile u;
+    u.b = item % nbatch;
+    const int tile = item / nbatch, i = tile / ntr;
+    u.kx0 = (tile - i * ntr) * TX;
+    u.ky = row_of(i, g.My);
+    u.ncol = min(TX, H - u.kx0);
+    u.col0 = u.ky * H + u.kx0;                  // < My H < 2^31 (checked at launch)
+    return u;
+  };
+  // the input planes of a tile into the staging buffer (asynchronous;
+  // thread t copies column t % TX)
+  auto prefetch = [&](int item) {
+    const Tile u = tile_of(item);
+    if (c < u.ncol) {
+      const C* src = data + (int64_t)u.b * 6 * gstride + u.col0 + c;
 #pragma unroll
       for (int grid = 0; grid < 3; ++grid)
         for (int z = j; z < Lz; z += NT / TX)
@@ -329,14 +354,14 @@ __global__ void __launch_bounds__(RA * TX, 3) k_zpass_pipe(Geom g, C* __restrict
   if (t == 0) s_item[0] = atomicAdd(queue, 1);
   __syncthreads();
   int item = s_item[0];
-  if (item < nitems) prefetch(item, 0);
+  if (item < nitems) prefetch(item);
   while (item < nitems) {
     // the tile after this one (read by all threads after the barriers below;
     // the slot was last read in the previous tile)
     if (t == 0) s_item[par ^ 1] = atomicAdd(queue, 1);
-    const int b = item % nbatch;
-    const int ncol = min(TX, (int)(zstride - (int64_t)(item / nbatch) * TX));
-    C* base = data + (int64_t)b * 6 * gstride;
+    const Tile u = tile_of(item);
+    const int ncol = u.ncol;
+    C* base = data + (int64_t)u.b * 6 * gstride + u.col0;
     cp_async_wait_all();
     __syncthreads();                            // staging and columns of this tile in; buffer free
 
@@ -352,13 +377,24 @@ __global__ void __launch_bounds__(RA * TX, 3) k_zpass_pipe(Geom g, C* __restrict
         [&](int line, int pos, C v) { buf[pos * LD + line] = v; });
     __syncthreads();                            // buffer complete, staging free
     const int next = s_item[par ^ 1];
-    if (next < nitems) prefetch(next, par ^ 1);
+    if (next < nitems) prefetch(next);
 
-    // ---- last forward stage (radix RB) into registers, sources scaled by s_b
-    const int ky = coly[par * TX + c];
-    const int kx = colz[par * TX + c] - ky * H;
-    const bool fy = ky > g.My / 2;
+    // blocked-spectra offsets of the thread's frequencies (kz folded, ky
+    // folded, kx; a column past the row's end reads column kx0's values,
+    // computed and never stored); the 6 potential kernels are loaded now,
+    // ahead of the stage below
+    const bool fy = u.ky > g.My / 2;
     const float sy = fy ? -1.f : 1.f;
+    const int sb = spec_block(g, nm, fy ? g.My - u.ky : u.ky, u.kx0 + (c < ncol ? c : 0));
+    int off[RB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      const int kz = j + r * RA;
+      off[r] = (kz > L / 2 ? L - kz : kz) * (kNumKernels * kSpecBlk) + sb;
+    }
+    float kp[6][RB];
+    load_pot<RB>(spec, off, kp);
+    // ---- last forward stage (radix RB) into registers, sources scaled by s_b
     C S[3][RB];
 #pragma unroll
     for (int be = 0; be < 3; ++be) {
@@ -371,17 +407,6 @@ __global__ void __launch_bounds__(RA * TX, 3) k_zpass_pipe(Geom g, C* __restrict
       for (int r = 0; r < RB; ++r)
         S[be][r] = be == 0 ? v[r] : be == 1 ? cscale(v[r], sy) : cmul(v[r], phs[j + r * RA]);
     }
-    // kernel-octant offsets of the thread's frequencies (kz folded, ky folded, kx)
-    const int rec0 = (fy ? g.My - ky : ky) * H + kx;
-    const int zrec = g.Oy * H;
-    int off[RB];
-#pragma unroll
-    for (int r = 0; r < RB; ++r) {
-      const int kz = j + r * RA;
-      off[r] = (kz > L / 2 ? L - kz : kz) * zrec + rec0;
-    }
-    float ka[RB][3], kb[RB][3];
-    load_kv<0, 0, RB>(spec, otot, off, ka);
     __syncthreads();                            // every stage-B input read: the buffer takes the outputs
 
     // last inverse stage (radix RA with twiddles, outputs below Mz/2) of
@@ -399,27 +424,26 @@ __global__ void __launch_bounds__(RA * TX, 3) k_zpass_pipe(Geom g, C* __restrict
         dft<RA, C>(v, true);
         const int grid = line / TX + 3 * h, cc = line % TX;
         if (cc < ncol) {
-          C* o = base + grid * gstride + colz[par * TX + cc] + jj * zstride;
+          C* o = base + grid * gstride + cc + jj * zstride;
 #pragma unroll
           for (int r = 0; r < RA / 2; ++r)
             if (jj + r * NB < Lz) o[(int64_t)r * NB * zstride] = v[r];
         }
       }
     };
-    // ---- potential outputs; kernel values loaded one grid ahead
-    load_kv<0, 1, RB>(spec, otot, off, kb);
-    mac_store<0, 0, RA, RB, TX, LD>(ka, S, sy, j, c, ph, phs, buf);
-    load_kv<0, 2, RB>(spec, otot, off, ka);
-    mac_store<0, 1, RA, RB, TX, LD>(kb, S, sy, j, c, ph, phs, buf);
-    mac_store<0, 2, RA, RB, TX, LD>(ka, S, sy, j, c, ph, phs, buf);
+    // ---- potential outputs
+    mac_store_pot<0, RA, RB, TX, LD>(kp, S, sy, j, c, ph, phs, buf);
+    mac_store_pot<1, RA, RB, TX, LD>(kp, S, sy, j, c, ph, phs, buf);
+    mac_store_pot<2, RA, RB, TX, LD>(kp, S, sy, j, c, ph, phs, buf);
     __syncthreads();
     last_stage(0);
+    float ka[RB][3], kb[RB][3];
+    load_kv<1, 0, RB>(spec, off, ka);
     __syncthreads();                            // the buffer takes the field outputs
-    // ---- field outputs
-    load_kv<1, 0, RB>(spec, otot, off, ka);
-    load_kv<1, 1, RB>(spec, otot, off, kb);
+    // ---- field outputs; kernel values loaded one grid ahead
+    load_kv<1, 1, RB>(spec, off, kb);
     mac_store<1, 0, RA, RB, TX, LD>(ka, S, sy, j, c, ph, phs, buf);
-    load_kv<1, 2, RB>(spec, otot, off, ka);
+    load_kv<1, 2, RB>(spec, off, ka);
     mac_store<1, 1, RA, RB, TX, LD>(kb, S, sy, j, c, ph, phs, buf);
     mac_store<1, 2, RA, RB, TX, LD>(ka, S, sy, j, c, ph, phs, buf);
     __syncthreads();
@@ -436,13 +460,13 @@ int launch_zpipe(const Handle& h, C* data, int B, cudaStream_t st) {
   const Plan1D<float2>& pz = h.pzf[0];
   const Plan1D<float2>& pv = h.pzfr[0];
   constexpr int L = RA * RB, NT = RA * TX;
-  const size_t sm = ((size_t)L * 3 * TX + (size_t)3 * (L / 2) * TX + pz.twn + pv.twn + 2 * L) * sizeof(C) +
-                    4 * TX * sizeof(int);
-  const int64_t cols = (int64_t)g.My * g.Hx;
-  const int64_t items = (cols + TX - 1) / TX * B;
-  VC_CHECK(items < ((int64_t)1 << 31) && cols + TX < ((int64_t)1 << 31) &&
-               (int64_t)g.Hx * g.Oy * g.Oz * kNumKernels < ((int64_t)1 << 31),
+  const size_t sm = ((size_t)L * 3 * TX + (size_t)3 * (L / 2) * TX + pz.twn + pv.twn + 2 * L) * sizeof(C);
+  const int nm = (g.Hx + kSpecBlk - 1) / kSpecBlk;
+  const int64_t items = (int64_t)g.My * ((g.Hx + TX - 1) / TX) * B;
+  VC_CHECK(items < ((int64_t)1 << 31) && (int64_t)g.My * g.Hx < ((int64_t)1 << 31) &&
+               (int64_t)g.Oy * nm * g.Oz * kNumKernels * kSpecBlk < ((int64_t)1 << 31),
            VOXCAP_ERR_UNSUPPORTED, "grid too large for the compiled z pass");
+  VC_CHECK(h.spec_fb.p != nullptr && TX % kSpecBlk == 0, VOXCAP_ERR_UNSUPPORTED, "blocked spectra missing");
   VC_CHECK(2 * g.Lz <= L && g.My % 2 == 0, VOXCAP_ERR_UNSUPPORTED, "z padding shorter than twice the grid or odd My");
   auto kern = k_zpass_pipe<RA, RB, TX>;
   VC_TRY(set_smem(kern, sm));
@@ -453,8 +477,8 @@ int launch_zpipe(const Handle& h, C* data, int B, cudaStream_t st) {
   const int grid = (int)std::min<int64_t>(items, (int64_t)per_sm * sms);
   VC_CHECK(h.zqueue.p != nullptr, VOXCAP_ERR_UNSUPPORTED, "tile counter of the persistent z pass missing");
   VC_CUDA(cudaMemsetAsync(h.zqueue.p, 0, sizeof(int), st));
-  kern<<<grid, NT, sm, st>>>(g, data, h.spec_f.p, (int)((int64_t)g.Hx * g.Oy * g.Oz), pz.stw, pz.twn,
-                             pz.twoff[1], pv.stw, pv.twn, pv.twoff[1], h.phf[2], B, (int)items, h.zqueue.p);
+  kern<<<grid, NT, sm, st>>>(g, data, h.spec_fb.p, nm, pz.stw, pz.twn, pz.twoff[1], pv.stw, pv.twn,
+                             pv.twoff[1], h.phf[2], B, (int)items, h.zqueue.p);
   ::vc::note_launch();
   VC_CUDA(cudaGetLastError());
   return VOXCAP_OK;
@@ -466,18 +490,18 @@ int launch_z(const Handle& h, C* data, int B, cudaStream_t st) {
   const Plan1D<float2>& pz = h.pzf[0];
   const Plan1D<float2>& pv = h.pzfr[0];
   constexpr int L = RA * RB;
-  const size_t sm = ((size_t)L * 3 * TX + (size_t)3 * RB * RA * TX + pz.twn + pv.twn + L) * sizeof(C) +
-                    2 * TX * sizeof(int);
-  const int64_t cols = (int64_t)g.My * g.Hx;
-  const int64_t tiles = (cols + TX - 1) / TX;
-  VC_CHECK(tiles * B < ((int64_t)1 << 31) && (int64_t)g.Hx * g.Oy * g.Oz * kNumKernels < ((int64_t)1 << 31),
+  const size_t sm = ((size_t)L * 3 * TX + (size_t)3 * RB * RA * TX + pz.twn + pv.twn + L) * sizeof(C);
+  const int nm = (g.Hx + kSpecBlk - 1) / kSpecBlk;
+  const int64_t tiles = (int64_t)g.My * ((g.Hx + TX - 1) / TX);
+  VC_CHECK(tiles * B < ((int64_t)1 << 31) && (int64_t)g.My * g.Hx < ((int64_t)1 << 31) &&
+               (int64_t)g.Oy * nm * g.Oz * kNumKernels * kSpecBlk < ((int64_t)1 << 31),
            VOXCAP_ERR_UNSUPPORTED, "grid too large for the compiled z pass");
-  VC_CHECK(2 * g.Lz <= L && g.My % 2 == 0 && cols + TX < ((int64_t)1 << 31), VOXCAP_ERR_UNSUPPORTED,
-           "z padding shorter than twice the grid, odd My or too many columns");
+  VC_CHECK(2 * g.Lz <= L && g.My % 2 == 0, VOXCAP_ERR_UNSUPPORTED, "z padding shorter than twice the grid or odd My");
+  VC_CHECK(h.spec_fb.p != nullptr && TX % kSpecBlk == 0, VOXCAP_ERR_UNSUPPORTED, "blocked spectra missing");
   auto kern = k_zpass_fast<RA, RB, TX>;
   VC_TRY(set_smem(kern, sm));
-  kern<<<(unsigned)(tiles * B), RA * TX, sm, st>>>(g, data, h.spec_f.p, (int)((int64_t)g.Hx * g.Oy * g.Oz), pz.stw,
-                                                   pz.twn, pz.twoff[1], pv.stw, pv.twn, pv.twoff[1], h.phf[2], B);
+  kern<<<(unsigned)(tiles * B), RA * TX, sm, st>>>(g, data, h.spec_fb.p, nm, pz.stw, pz.twn, pz.twoff[1], pv.stw,
+                                                   pv.twn, pv.twoff[1], h.phf[2], B);
   ::vc::note_launch();
   VC_CUDA(cudaGetLastError());
   return VOXCAP_OK;

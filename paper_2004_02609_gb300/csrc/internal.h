@@ -175,6 +175,8 @@ struct GmresGraph {
   GmresGraph& operator=(const GmresGraph&) = delete;
 };
 
+constexpr int kSpecBlk = 8;      // kx columns per block of the blocked FP32 spectra
+
 struct Handle {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -223,6 +225,10 @@ struct Handle {
   DBuf<double> toep[kNumKernels];
   DBuf<double> spec_d;            // [15][Oz][Oy][Hx] real, scaled by 1/(Mx My Mz)
   DBuf<float> spec_f;
+  // the same FP32 spectra in blocks of kSpecBlk consecutive kx for the
+  // compiled z pass: [Oy][ceil(Hx / kSpecBlk)][Oz][15][kSpecBlk] (zero past
+  // Hx), so that the spectra of a tile of columns are one contiguous block
+  DBuf<float> spec_fb;
   // MVM workspace
   int ws_batch = 0;
   DBuf<char> ws;                  // raw workspace

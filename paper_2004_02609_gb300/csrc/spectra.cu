@@ -18,6 +18,7 @@
 #include <cstring>
 #include <vector>
 
+#include "fast.cuh"
 #include "internal.h"
 
 namespace vc {
@@ -357,7 +358,7 @@ template <typename T>
 __global__ void k_extract(const C_t<T>* __restrict__ spec, int64_t Htot, Geom g, int k0,
                           const double2* __restrict__ phx, const double2* __restrict__ phy,
                           const double2* __restrict__ phz, double scale,
-                          double* __restrict__ Rd, float* __restrict__ Rf) {
+                          double* __restrict__ Rd, float* __restrict__ Rf, float* __restrict__ Rb) {
   const int b = blockIdx.y, kk = k0 + b;
   const int te = ker_test(kk), so = ker_src(kk);
   const bool E = kk >= 6;
@@ -380,6 +381,10 @@ __global__ void k_extract(const C_t<T>* __restrict__ spec, int64_t Htot, Geom g,
   r *= scale;
   Rd[kk * n + t] = r;
   Rf[kk * n + t] = (float)r;
+  if (Rb) {
+    const int nm = (g.Hx + kSpecBlk - 1) / kSpecBlk, m = kx / kSpecBlk;
+    Rb[((((int64_t)ky * nm + m) * g.Oz + kz) * kNumKernels + kk) * kSpecBlk + kx % kSpecBlk] = (float)r;
+  }
 }
 
 // largest power-of-two line count (<= maxlines) whose two buffers fit in 96 KB
@@ -410,6 +415,13 @@ static int spectra_impl(Handle& h) {
   VC_TRY(spec.alloc((size_t)Htot * nb));
   VC_TRY(h.spec_d.alloc((size_t)Otot * kNumKernels));
   VC_TRY(h.spec_f.alloc((size_t)Otot * kNumKernels));
+  float* blocked = nullptr;
+  if (fast_z_ok(h)) {
+    const size_t nblk = (size_t)g.Oy * ((g.Hx + kSpecBlk - 1) / kSpecBlk) * g.Oz * kNumKernels * kSpecBlk;
+    VC_TRY(h.spec_fb.alloc(nblk));
+    VC_CUDA(cudaMemsetAsync(h.spec_fb.p, 0, nblk * sizeof(float), h.stream));
+    blocked = h.spec_fb.p;
+  }
   EmbedSet es;
   for (int kk = 0; kk < kNumKernels; ++kk) {
     es.T[kk] = h.toep[kk].p;
@@ -471,7 +483,8 @@ static int spectra_impl(Handle& h) {
       VC_CUDA(cudaGetLastError());
     }
     k_extract<T><<<dim3((unsigned)((Otot + TB - 1) / TB), nk), TB, 0, h.stream>>>(
-        spec.p, Htot, g, k0, h.phd[0], h.phd[1], h.phd[2], scale, h.spec_d.p, h.spec_f.p); ::vc::note_launch();
+        spec.p, Htot, g, k0, h.phd[0], h.phd[1], h.phd[2], scale, h.spec_d.p, h.spec_f.p, blocked);
+    ::vc::note_launch();
     VC_CUDA(cudaGetLastError());
   }
   return VOXCAP_OK;
