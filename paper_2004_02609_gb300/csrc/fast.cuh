@@ -128,17 +128,24 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // input lines are zero from position L / 2 on (those entries of buf are
 // never read); HOUT: only positions < L / 2 of the result are used (the
 // last stage leaves the others unwritten).
-template <typename P, int TX, int NT, bool INV, int PT = TX, bool HIN = false, bool HOUT = false>
-__device__ __forceinline__ void transform_inplace(C* buf, const C* __restrict__ tw, int off2, int off3) {
+// transform_inplace_ld: the same with the first stage's inputs from ld(c, pos).
+template <typename P, int TX, int NT, bool INV, int PT = TX, bool HIN = false, bool HOUT = false, typename Ld>
+__device__ __forceinline__ void transform_inplace_ld(C* buf, const C* __restrict__ tw, int off2, int off3, Ld ld) {
   constexpr int RL = P::NST == 3 ? P::R3 : P::R2;
   constexpr int ROUT = HOUT ? (RL + 1) / 2 : RL;
-  stage_inplace<P::L, P::R1, 1, TX, NT, INV, PT, HIN ? P::R1 / 2 : P::R1>(buf, tw);
+  stage_inplace_ld<P::L, P::R1, 1, TX, NT, INV, PT, HIN ? P::R1 / 2 : P::R1>(buf, tw, ld);
   if constexpr (P::NST == 3) {
     stage_inplace<P::L, P::R2, P::R1, TX, NT, INV, PT>(buf, tw + off2);
     stage_inplace<P::L, P::R3, P::R1 * P::R2, TX, NT, INV, PT, P::R3, ROUT>(buf, tw + off3);
   } else {
     stage_inplace<P::L, P::R2, P::R1, TX, NT, INV, PT, P::R2, ROUT>(buf, tw + off2);
   }
+}
+
+template <typename P, int TX, int NT, bool INV, int PT = TX, bool HIN = false, bool HOUT = false>
+__device__ __forceinline__ void transform_inplace(C* buf, const C* __restrict__ tw, int off2, int off3) {
+  transform_inplace_ld<P, TX, NT, INV, PT, HIN, HOUT>(buf, tw, off2, off3,
+                                                      [&](int c, int pos) -> C { return buf[pos * PT + c]; });
 }
 
 // copy n complex values to shared memory (caller synchronises)

@@ -103,31 +103,31 @@ static int tune(Handle& h, bool use_cache) {
     }
     h.ytx[which] = best_y;
   }
-  // then the compiled-plan passes, where the lengths have a plan (two tile
-  // widths for the longest y plan)
+  // then the compiled-plan passes, where the lengths have a plan, in every
+  // combination of their variant switches (the persistent z pass, the
+  // persistent forward and inverse y passes)
   if (fast_plan_ok(h.pf[1]) || fast_z_ok(h) || fast_x_ok(h)) {
-    // the compiled passes with their default variants, then each variant
-    // switch kept where it is faster (the persistent z pass, the persistent
-    // forward and inverse y passes)
     const bool ypipe = fast_plan_ok(h.pf[1]);
     const bool zpipe = fast_z_ok(h) && h.pzf[0].radix[0] == 16;
-    h.path = 1;
-    float ms;
-    VC_TRY(time_products(&ms));
-    if (ms >= 0.0f && ms < best_ms) {
-      best_ms = ms;
-      int* sw[3] = {&h.zfvar, &h.yvar[0], &h.yvar[1]};
-      const bool avail[3] = {zpipe, ypipe, ypipe};
-      for (int k = 0; k < 3; ++k) {
-        if (!avail[k]) continue;
-        *sw[k] = 1;
-        VC_TRY(time_products(&ms));
-        if (ms >= 0.0f && ms < best_ms) best_ms = ms;
-        else *sw[k] = 0;
+    int best_bits = -1;
+    for (int bits = 0; bits < 8; ++bits) {
+      if (((bits & 1) && !zpipe) || ((bits & 6) && !ypipe)) continue;
+      h.path = 1;
+      h.zfvar = bits & 1;
+      h.yvar[0] = (bits >> 1) & 1;
+      h.yvar[1] = (bits >> 2) & 1;
+      float ms;
+      VC_TRY(time_products(&ms));
+      if (ms >= 0.0f && ms < best_ms) {
+        best_ms = ms;
+        best_bits = bits;
       }
-    } else {
-      h.path = 0;
     }
+    const int bb = best_bits > 0 ? best_bits : 0;
+    h.path = best_bits >= 0 ? 1 : 0;
+    h.zfvar = bb & 1;
+    h.yvar[0] = (bb >> 1) & 1;
+    h.yvar[1] = (bb >> 2) & 1;
   }
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune[key] = {h.zvar, h.ztx, h.ytx[0], h.ytx[1], h.path, h.yvar[0], h.yvar[1], h.zfvar};
