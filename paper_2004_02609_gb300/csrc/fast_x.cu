@@ -1,16 +1,19 @@
 // x passes of the forward FP32 product (Eqs. 9-11) on compiled plans.
 //
-// xfwd: the panel charges of each face row are scattered straight from the
-// panel list (every row of the canonical order is one contiguous run of
-// conductor panels and one of dielectric panels) onto a zeroed line in
-// shared memory -- two real rows per complex line --, the line is
+// xfwd: the panel charges of the tile's face rows are scattered straight
+// from the panel list (the rows are consecutive in the canonical order, so
+// their conductor panels are one contiguous run and their dielectric panels
+// another) onto zeroed lines in shared memory -- two real rows per complex
+// line --, the line is
 // transformed along x, and the half spectra of the two rows are split out,
 // given the half-voxel phase of the x grid and written to HBM (row-
 // contiguous, coalesced).
-// xinv: the potential and field half spectra of an output row are read
-// (coalesced), extended to the full Hermitian line as potential + i field,
-// transformed back, and gathered at the row's panels: a conductor row takes
-// the potential, a dielectric row I' x + the field (Eq. 4).
+// xinv: the potential and field half spectra of the tile's output rows are
+// copied into shared memory by cp.async (contiguous runs, all in flight at
+// once), extended to the full Hermitian line as potential + i field by the
+// first stage as it reads them, transformed back, and gathered at the row's
+// panels: a conductor row takes the potential, a dielectric row I' x + the
+// field (Eq. 4).
 // NL lines share one shared-memory buffer with a pitch of NL + 1 complex
 // values, so that reads along x by consecutive lanes avoid bank conflicts.
 // The padded length is at least twice the row length: the forward transform
@@ -54,21 +57,33 @@ __global__ void __launch_bounds__(NT) k_xfwd_fast(XArgs a, const float* __restri
   const int nlines = (g.Ly + 1) / 2;         // two rows per complex line
   const int l0 = blockIdx.x * NL;
   const float* xr = x + (int64_t)r * a.N;
+  // the tile's rows y0 .. y0 + nrows - 1 are consecutive in the canonical
+  // order, so their panels of each kind are one contiguous range; the row
+  // starts go to shared memory first
+  __shared__ int rs[2][2 * NL + 1];
+  const int y0 = 2 * l0;
+  const int nrows = min(2 * NL, g.Ly - y0);
+  const int64_t row0 = ((int64_t)grid * g.Lz + z) * g.Ly + y0;
+  for (int i = threadIdx.x; i < 2 * (nrows + 1); i += NT) {
+    const int kind = i / (nrows + 1), k = i - kind * (nrows + 1);
+    rs[kind][k] = a.rstart[(2 * (int64_t)s + kind) * a.R + row0 + k];
+  }
   for (int i = threadIdx.x; i < (L / 2) * PT; i += NT) buf[i] = mk<C>(0.f, 0.f);   // the upper half is never read
   __syncthreads();
-  // scatter: one warp per row (2 NL rows), lanes over the row's panels
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // scatter: threads over the tile's panels of each kind (independent,
+  // coalesced loads); a panel's row by bisection of the row starts
   float* fb = reinterpret_cast<float*>(buf);
-  for (int rr = warp; rr < 2 * NL; rr += NT / 32) {
-    const int l = rr >> 1, part = rr & 1;
-    const int y = 2 * (l0 + l) + part;
-    if (l0 + l >= nlines || y >= g.Ly) continue;
-    const int64_t row = ((int64_t)grid * g.Lz + z) * g.Ly + y;
 #pragma unroll
-    for (int kind = 0; kind < 2; ++kind) {
-      const int64_t q = (2 * (int64_t)s + kind) * a.R + row;
-      const int p1 = a.rstart[q + 1];
-      for (int p = a.rstart[q] + lane; p < p1; p += 32) fb[2 * (a.px[p] * PT + l) + part] = xr[p];
+  for (int kind = 0; kind < 2; ++kind) {
+    const int* rk = rs[kind];
+    for (int p = rk[0] + threadIdx.x; p < rk[nrows]; p += NT) {
+      int lo = 0, hi = nrows;                   // rk[lo] <= p < rk[hi]
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (rk[mid] <= p) lo = mid;
+        else hi = mid;
+      }
+      fb[2 * (a.px[p] * PT + (lo >> 1)) + (lo & 1)] = xr[p];
     }
   }
   __syncthreads();
@@ -99,9 +114,10 @@ __global__ void __launch_bounds__(NT) k_xinv_fast(XArgs a, const C* __restrict__
                                                   int off2, int off3, const C* __restrict__ phx) {
   using P = fast::Plan<R1, R2, R3>;
   constexpr int L = P::L, H = L / 2 + 1, PT = NL + 1;
+  constexpr int BUFN = L * PT > 2 * NL * H ? L * PT : 2 * NL * H;   // the transform, or the raw rows
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
-  C* tws = buf + L * PT;
+  C* tws = buf + BUFN;
   C* phs = tws + twn;                 // half-voxel phases of the x grid
   fast::load_table<NT>(tws, stw, twn);
   fast::load_table<NT>(phs, phx, H);
@@ -114,59 +130,59 @@ __global__ void __launch_bounds__(NT) k_xinv_fast(XArgs a, const C* __restrict__
   const int64_t plane = (int64_t)g.Ly * H;
   const C* srcA = in + (((int64_t)b * 6 + al) * g.Lz + z) * plane;        // potential
   const C* srcB = in + (((int64_t)b * 6 + 3 + al) * g.Lz + z) * plane;    // field
-  __syncthreads();                                                        // tables loaded
-  // Hermitian extension of potential + i field, lanes along x: each half-
-  // spectrum value k is read once and gives line entries k and L - k; the
-  // loads of U items are issued before any of them is used
-  constexpr int TOT = H * NL, IT = (TOT + NT - 1) / NT, U = 6;
-#pragma unroll
-  for (int i0 = 0; i0 < IT; i0 += U) {
-    C A[U], B[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int t = (i0 + u) * NT + (int)threadIdx.x;
-      A[u] = B[u] = mk<C>(0.f, 0.f);
-      if (i0 + u < IT && t < TOT) {
-        const int l = t / H, k = t - l * H;
-        if (l0 + l < g.Ly) {
-          const int64_t ro = (int64_t)(l0 + l) * H + k;
-          A[u] = srcA[ro];
-          B[u] = srcB[ro];
-        }
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int t = (i0 + u) * NT + (int)threadIdx.x;
-      if (i0 + u < IT && t < TOT) {
-        const int l = t / H, k = t - l * H;
-        C a = A[u], b = B[u];
-        if (al == 0) {
-          const C ph = cconj(phs[k]);
-          a = cmul(a, ph);
-          b = cmul(b, ph);
-        }
-        buf[k * PT + l] = cadd(a, cmul_pi(b));
-        if (k > 0 && k < L / 2) buf[(L - k) * PT + l] = cadd(cconj(a), cmul_pi(cconj(b)));
-      }
-    }
+  // the potential and field half spectra of the tile's rows (each a
+  // contiguous run of nl H values) into the buffer by cp.async, every copy in
+  // flight at once: potential at buf[l H + k], field at buf[(NL + l) H + k]
+  const int nl = min(NL, g.Ly - l0);
+  // row starts of the tile's rows, for the gather
+  __shared__ int rs[2][NL + 1];
+  const int64_t row0 = ((int64_t)al * g.Lz + z) * g.Ly + l0;
+  for (int i = threadIdx.x; i < 2 * (nl + 1); i += NT) {
+    const int kind = i / (nl + 1), k = i - kind * (nl + 1);
+    rs[kind][k] = a.rstart[(2 * (int64_t)s + kind) * a.R + row0 + k];
   }
-  __syncthreads();
-  fast::transform_inplace<P, NL, NT, true, PT, false, true>(buf, tws, off2, off3);
-  // gather at the panels of each row: one warp per row
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int e = threadIdx.x; e < nl * H; e += NT) {
+    fast::cp_async8(&buf[e], srcA + (int64_t)l0 * H + e);
+    fast::cp_async8(&buf[NL * H + e], srcB + (int64_t)l0 * H + e);
+  }
+  fast::cp_async_commit();
+  fast::cp_async_wait_all();
+  __syncthreads();                                                        // tables and rows loaded
+  // Hermitian extension of potential + i field, built by the first stage as
+  // it reads (value k gives line entries k and L - k)
+  fast::transform_inplace_ld<P, NL, NT, true, PT, false, true>(buf, tws, off2, off3, [&](int l, int pos) -> C {
+    if (l >= nl) return mk<C>(0.f, 0.f);
+    const int k = pos <= L / 2 ? pos : L - pos;
+    C A = buf[l * H + k], B = buf[(NL + l) * H + k];
+    if (al == 0) {
+      const C ph = cconj(phs[k]);
+      A = cmul(A, ph);
+      B = cmul(B, ph);
+    }
+    if (pos > L / 2) {
+      A = cconj(A);
+      B = cconj(B);
+    }
+    return cadd(A, cmul_pi(B));
+  });
+  // gather at the panels of the tile's rows (consecutive in the canonical
+  // order: one contiguous range per kind), threads over the panels, a
+  // panel's row by bisection of the row starts
   const float* xr = x + (int64_t)r * a.N;
   float* yr = y + (int64_t)r * a.N;
-  for (int l = warp; l < NL; l += NT / 32) {
-    const int yy = l0 + l;
-    if (yy >= g.Ly) continue;
-    const int64_t row = ((int64_t)al * g.Lz + z) * g.Ly + yy;
-    const int64_t qc = (2 * (int64_t)s) * a.R + row;
-    const int64_t qd = (2 * (int64_t)s + 1) * a.R + row;
-    for (int p = a.rstart[qc] + lane, p1 = a.rstart[qc + 1]; p < p1; p += 32)
-      yr[p] = buf[a.px[p] * PT + l].x;
-    for (int p = a.rstart[qd] + lane, p1 = a.rstart[qd + 1]; p < p1; p += 32)
-      yr[p] = a.idiag[p] * xr[p] + buf[a.px[p] * PT + l].y;
+#pragma unroll
+  for (int kind = 0; kind < 2; ++kind) {
+    const int* rk = rs[kind];
+    for (int p = rk[0] + threadIdx.x; p < rk[nl]; p += NT) {
+      int lo = 0, hi = nl;                      // rk[lo] <= p < rk[hi]
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (rk[mid] <= p) lo = mid;
+        else hi = mid;
+      }
+      const C v = buf[a.px[p] * PT + lo];
+      yr[p] = kind == 0 ? v.x : a.idiag[p] * xr[p] + v.y;   // conductor: potential; dielectric: Eq. 4
+    }
   }
 }
 
@@ -205,8 +221,9 @@ template <int R1, int R2, int R3, int NL, int NT>
 int launch_xinv(const Handle& h, const C* in, const float* x, float* y, int nrhs, cudaStream_t st) {
   const Geom& g = h.g;
   const Plan1D<float2>& p = h.pf[0];
-  constexpr int L = R1 * R2 * R3;
-  const size_t sm = ((size_t)L * (NL + 1) + p.twn + L / 2 + 1) * sizeof(C);
+  constexpr int L = R1 * R2 * R3, H = L / 2 + 1;
+  constexpr int BUFN = L * (NL + 1) > 2 * NL * H ? L * (NL + 1) : 2 * NL * H;
+  const size_t sm = ((size_t)BUFN + p.twn + H) * sizeof(C);
   VC_CHECK(2 * g.Lx <= L, VOXCAP_ERR_UNSUPPORTED, "x padding shorter than twice the grid");
   auto kern = k_xinv_fast<R1, R2, R3, NL, NT>;
   VC_TRY(set_smem(kern, sm));

@@ -215,7 +215,7 @@ int dispatch_y(const Handle& h, int G, const C* in, C* out, int64_t ibs, int64_t
     if (r[0] == 16 && r[1] == 9) VC_Y(16, 9, 1, 16, 144, 16, 144);
   } else if (p.nst == 3 && r[2] == 9) {
     if (r[0] == 8 && r[1] == 4) VC_Y(8, 4, 9, 16, 288, 16, 288);
-    if (r[0] == 16 && r[1] == 4) VC_Y(16, 4, 9, 16, 288, 8, 288);
+    if (r[0] == 16 && r[1] == 4) VC_Y(16, 4, 9, 16, 288, 8, 576);
     if (r[0] == 16 && r[1] == 8) VC_Y(16, 8, 9, 16, 576, 8, 576);
   }
 #undef VC_Y
