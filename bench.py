@@ -22,7 +22,8 @@ the adjoint gradient), the oracle's CPU time, clocks and the kernel-launch
 count.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-  python bench.py --products --workload bus [--path 0|1]   (product timing only)
+  python bench.py --products --workload bus [--path P]     (product timing only;
+                                                            meanders256: a profiling size)
   python bench.py --setup --workload pillars                (set-up timing only)
 
 Under torchrun (N > 1) every rank runs its own replica of the workload
@@ -69,6 +70,9 @@ def workload(name):
     if name == "meanders":
         return W.meanders(), ("two interleaved meanders (width 4, spacing 4, thickness 8, 32 legs) "
                               "in eps_r=3.9, 512x512x64 grid")
+    if name == "meanders256":
+        return W.meanders(256, 256, 64, 16), ("two interleaved meanders (width 4, spacing 4, thickness 8, "
+                                              "16 legs) in eps_r=3.9, 256x256x64 grid (profiling size)")
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -638,7 +642,7 @@ def main():
     ap.add_argument("--products", action="store_true",
                     help="time only the batched FP32 products of the workload (profiling aid)")
     ap.add_argument("--path", type=int, default=-1,
-                    help="with --products: FP32 product kernels 0 generic, 1 compiled plans, -1 tuned")
+                    help="with --products: FP32 product kernels 0 generic, 1 compiled plans (+ variant bits), -1 tuned")
     ap.add_argument("--setup", action="store_true",
                     help="time only the set-up of the workload, Tucker-restored and generated (profiling aid)")
     args = ap.parse_args()

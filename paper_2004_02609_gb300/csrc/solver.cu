@@ -177,6 +177,25 @@ __global__ void k_sub(const T* __restrict__ b, const T* __restrict__ ax, T* __re
   if (t < n) r[t] = b[t] - ax[t];
 }
 
+// r = b - ax with ax from an FP32 product
+__global__ void k_sub_f32(const double* __restrict__ b, const float* __restrict__ ax, double* __restrict__ r,
+                          int64_t n) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) r[t] = b[t] - (double)ax[t];
+}
+
+// r = b - ax in the columns whose mask is set; the others keep r
+__global__ void k_sub_cols(const double* __restrict__ b, const double* __restrict__ ax, double* __restrict__ r,
+                           int64_t N, int nrhs, const int* __restrict__ mask) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < N * nrhs && mask[t / N]) r[t] = b[t] - ax[t];
+}
+
+__global__ void k_to_f32(const double* __restrict__ src, float* __restrict__ dst, int64_t n) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) dst[t] = (float)src[t];
+}
+
 __global__ void k_cast_scaled(const double* __restrict__ src, float* __restrict__ dst, int64_t N, int nrhs,
                               const double* __restrict__ f) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -585,6 +604,7 @@ int solve(Handle& h, const double* B, int nrhs, double tol, double* X, voxcap_st
     return VOXCAP_OK;
   }
   DBuf<double> R64, AX, dpart, dnorm, fac;
+  DBuf<int> cmask;
   DBuf<float> rf, df;
   DBuf<double> d64;
   const size_t n = (size_t)N * nrhs;
@@ -593,6 +613,7 @@ int solve(Handle& h, const double* B, int nrhs, double tol, double* X, voxcap_st
   VC_TRY(dpart.alloc((size_t)nrhs * nchunks_for(N, nrhs) + 1));
   VC_TRY(dnorm.alloc(nrhs));
   VC_TRY(fac.alloc(nrhs));
+  VC_TRY(cmask.alloc(nrhs));
   if (refine) { VC_TRY(rf.alloc(n)); VC_TRY(df.alloc(n)); }
   else VC_TRY(d64.alloc(n));
   std::vector<double> bn, rn;
@@ -605,17 +626,47 @@ int solve(Handle& h, const double* B, int nrhs, double tol, double* X, voxcap_st
   double worst = 0.0;
   bool conv = false;
   int sweeps = 0;
+  // Under refinement the residual of a column whose last sweep only had to
+  // reach a large residual (expected relative residual >= 1e-5) is formed
+  // with an FP32 product: its error (~1e-7 of |b|) is two orders below that
+  // residual, so the next correction is as good as with an FP64 residual.
+  // Convergence is only ever decided on an FP64 residual, and each column's
+  // choice depends on its own history only (products are column by column).
+  std::vector<int> use32(nrhs, 0), need64(nrhs, 1);
   for (int sw = 0; sw <= max_sweeps; ++sw) {
     if (sw == 0) {
       VC_CUDA(cudaMemcpyAsync(R64.p, B, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      rn = bn;                                       // the first residual is B itself
     } else {
-      VC_TRY(mvm<double>(h, X, AX.p, nrhs, adjoint, nullptr));
-      cnt.matvecs += 1;
-      k_sub<double><<<gN, TB, 0, s>>>(B, AX.p, R64.p, (int64_t)n); ::vc::note_launch();
-      VC_CUDA(cudaGetLastError());
+      bool any32 = false, any64 = false;
+      for (int c = 0; c < nrhs; ++c) {
+        need64[c] = !use32[c];
+        any32 = any32 || use32[c];
+      }
+      if (any32) {
+        k_to_f32<<<gN, TB, 0, s>>>(X, rf.p, (int64_t)n); ::vc::note_launch();
+        VC_TRY(mvm<float>(h, rf.p, df.p, nrhs, adjoint, nullptr));
+        cnt.matvecs += 1;
+        k_sub_f32<<<gN, TB, 0, s>>>(B, df.p, R64.p, (int64_t)n); ::vc::note_launch();
+        VC_CUDA(cudaGetLastError());
+        VC_TRY(col_norms(h, R64.p, nrhs, rn, dpart.p, dnorm.p));
+        for (int c = 0; c < nrhs; ++c)               // close to the end: decide on FP64
+          if (use32[c] && bn[c] > 0.0 && rn[c] <= 10.0 * tol * bn[c]) need64[c] = 1;
+      }
+      for (int c = 0; c < nrhs; ++c) any64 = any64 || need64[c];
+      if (any64) {
+        VC_TRY(mvm<double>(h, X, AX.p, nrhs, adjoint, nullptr));
+        cnt.matvecs += 1;
+        if (any32) {
+          VC_CUDA(cudaMemcpyAsync(cmask.p, need64.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
+          k_sub_cols<<<gN, TB, 0, s>>>(B, AX.p, R64.p, N, nrhs, cmask.p); ::vc::note_launch();
+        } else {
+          k_sub<double><<<gN, TB, 0, s>>>(B, AX.p, R64.p, (int64_t)n); ::vc::note_launch();
+        }
+        VC_CUDA(cudaGetLastError());
+        VC_TRY(col_norms(h, R64.p, nrhs, rn, dpart.p, dnorm.p));
+      }
     }
-    if (sw == 0) rn = bn;                            // the first residual is B itself
-    else VC_TRY(col_norms(h, R64.p, nrhs, rn, dpart.p, dnorm.p));
     worst = 0.0;
     std::vector<double> f(nrhs), finv(nrhs), itol(nrhs);
     for (int c = 0; c < nrhs; ++c) {
@@ -638,6 +689,10 @@ int solve(Handle& h, const double* B, int nrhs, double tol, double* X, voxcap_st
     if (worst <= tol) { conv = true; break; }
     if (sw == max_sweeps || cnt.iters >= h.opts.max_iters) break;
     ++sweeps;
+    for (int c = 0; c < nrhs; ++c) {
+      const double rel = bn[c] > 0.0 ? rn[c] / bn[c] : 0.0;
+      use32[c] = refine && f[c] != 0.0 && rel * itol[c] >= 1e-5;
+    }
     int left = std::max(1, h.opts.max_iters - cnt.iters);
     VC_CUDA(cudaMemcpyAsync(fac.p, f.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
     if (refine) {
