@@ -223,7 +223,8 @@ def product_roofline(vc, dev, reps, workload_name):
         "kernel": "FP32 product, 5 passes (x scatter+R2C, y, z+spectral MAC+inverse z, inverse y, "
                   f"C2R+gather), {vc.n_conductors} columns, {workload_name}",
         "bound": "hbm", "achieved": b / t / 1e9, "peak": hbm, "unit": "GB/s",
-        "frac": b / t / 1e9 / hbm, "traffic": captured_traffic(workload_name),
+        "frac": b / t / 1e9 / hbm, "target_frac": 0.6, "target_met": b / t / 1e9 / hbm >= 0.6,
+        "traffic": captured_traffic(workload_name),
         "peak_source": peak_src, "bytes_per_launch": b, "launch_s": t,
         "fft_lengths": list(vc.fft_lengths()), "path": vc.set_product_path(-2)}
 

@@ -251,7 +251,7 @@ int dispatch_x(const Handle& h, const float* x, const C* in, C* out, float* y, i
   } else if (p.nst == 3 && r[2] == 9) {
     if (r[0] == 8 && r[1] == 4) VC_X(8, 4, 9, 16, 256);
     if (r[0] == 16 && r[1] == 4) VC_X(16, 4, 9, 16, 256);
-    if (r[0] == 16 && r[1] == 8) VC_X(16, 8, 9, 8, 256);
+    if (r[0] == 16 && r[1] == 8) VC_X(16, 8, 9, 16, 576);
   }
 #undef VC_X
   set_error("no compiled x-pass plan for this length");
