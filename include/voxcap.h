@@ -108,7 +108,7 @@ typedef struct voxcap_tucker {
 
 typedef struct voxcap_opts {
   int precision;       /* VOXCAP_FP64 or VOXCAP_FP32_REFINE (default) */
-  int restart;         /* GMRES restart length (default 35, Sec. III) */
+  int restart;         /* GMRES restart length (default 35, Sec. III; at most 512) */
   double inner_tol;    /* FP32 inner GMRES: tightest relative tolerance of one refinement sweep
                           (default 1e-4); a sweep stops earlier when that already meets tol */
   int max_iters;       /* cap on GMRES iterations per solve (default 2000) */

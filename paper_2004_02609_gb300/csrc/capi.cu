@@ -64,6 +64,8 @@ static int setup_impl(const int32_t* labels, int nx, int ny, int nz, int n_struc
   set_alloc_stream(h.stream);
   if (opts) h.opts = *opts; else voxcap_default_opts(&h.opts);
   if (h.opts.restart < 1) h.opts.restart = 35;
+  VC_CHECK(h.opts.restart <= kMaxRestart, VOXCAP_ERR_ARG,
+           "restart must be at most " + std::to_string(kMaxRestart));
   if (h.opts.max_iters < 1) h.opts.max_iters = 2000;
   VC_CHECK(h.opts.entries >= VOXCAP_ENTRIES_AUTO && h.opts.entries <= VOXCAP_ENTRIES_FAR32, VOXCAP_ERR_ARG,
            "entries must be one of VOXCAP_ENTRIES_*");

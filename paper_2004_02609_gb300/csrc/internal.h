@@ -175,6 +175,7 @@ struct GmresGraph {
   GmresGraph& operator=(const GmresGraph&) = delete;
 };
 
+constexpr int kMaxRestart = 512;   // longest GMRES restart cycle (Arnoldi basis of kMaxRestart + 1 vectors)
 constexpr int kSpecBlk = 8;      // kx columns per block of the blocked FP32 spectra
 
 struct Handle {

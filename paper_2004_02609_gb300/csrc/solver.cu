@@ -301,9 +301,14 @@ struct StepArgs {
 // blockIdx.x: pass 0: dots V_i . w -> hcol; pass 1: w -= sum hcol_i V_i, dots
 // -> hcol2; pass 2: w -= sum hcol2_i V_i, ||w||^2 -> nrm2, then the Givens
 // update of the column.  The last CTA of a column sums its partials.
+// Arithmetic: the basis precision T for the update and for each lane's
+// partial dot product (an FP32 basis is good to 6e-8 and a lane sums about
+// 20 terms; FP64 arithmetic is 64 times slower on this GPU), FP64 from the
+// lane sums on; the FP64 basis of the plain FP64 solve stays FP64 throughout.
 template <typename T>
 __global__ void k_gs_step(const T* __restrict__ V, T* __restrict__ w, int pass, GState s, StepArgs a) {
   __shared__ double sh[32];
+  __shared__ T cf[kMaxRestart + 1];
   const int col = blockIdx.y;
   const int chunk = blockIdx.x;
   if (!s.active[col]) return;                        // whole column: no CTA takes a ticket
@@ -316,10 +321,12 @@ __global__ void k_gs_step(const T* __restrict__ V, T* __restrict__ w, int pass, 
   const int64_t vstride = (int64_t)a.nrhs * N;
   if (pass > 0) {
     const double* coef = (pass == 1 ? s.hcol : s.hcol2) + (int64_t)col * (a.m + 1);
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) cf[i] = (T)coef[i];
+    __syncthreads();
     for (int64_t p = lo + threadIdx.x; p < hi; p += blockDim.x) {
-      double acc = (double)wc[p];
-      for (int i = 0; i < nv; ++i) acc -= coef[i] * (double)V[i * vstride + (int64_t)col * N + p];
-      wc[p] = (T)acc;
+      T acc = wc[p];
+      for (int i = 0; i < nv; ++i) acc -= cf[i] * V[i * vstride + (int64_t)col * N + p];
+      wc[p] = acc;
     }
     __syncthreads();
   }
@@ -328,8 +335,9 @@ __global__ void k_gs_step(const T* __restrict__ V, T* __restrict__ w, int pass, 
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int i = wid; i < nd; i += nw) {
     const T* vi = dot ? V + i * vstride + (int64_t)col * N : wc;
-    double acc = 0.0;
-    for (int64_t p = lo + lane; p < hi; p += 32) acc += (double)vi[p] * (double)wc[p];
+    T lacc = 0;
+    for (int64_t p = lo + lane; p < hi; p += 32) lacc += vi[p] * wc[p];
+    double acc = (double)lacc;
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if (lane == 0) a.partial[((int64_t)col * a.part_ld + i) * a.nchunks + chunk] = acc;
   }
