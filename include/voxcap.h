@@ -124,6 +124,13 @@ typedef struct voxcap_opts {
   const voxcap_tucker* tucker; /* NULL: generate the Toeplitz tensors (Eqs. 5-6, precision
                           per `entries`); else restore them from these Tucker
                           factors on the tensor cores (Sec. II.C), cropped to the grid */
+  int fast_refine;     /* FP32_REFINE only.  0 (default): FP64 in every refinement residual and
+                          in the Arnoldi orthogonalisation's arithmetic.  1: FP32 arithmetic
+                          for the FP32 basis's Gram-Schmidt updates and each lane's partial dot
+                          product (FP64 from the lane sums on), and an FP32 product for the
+                          residual of a column whose last sweep only had to reach a relative
+                          residual >= 1e-5; convergence is still decided on FP64 residuals.
+                          Faster on GPUs with slow FP64; C to about 1e-7 of the FP64 solve. */
 } voxcap_opts;
 
 typedef struct voxcap_stats {

@@ -34,6 +34,7 @@ void voxcap_default_opts(voxcap_opts* o) {
   o->pad_mode = 0;
   o->entries = VOXCAP_ENTRIES_AUTO;
   o->tucker = nullptr;
+  o->fast_refine = 0;
 }
 
 const char* voxcap_last_error(void) { return vc::last_error(); }

@@ -301,14 +301,15 @@ struct StepArgs {
 // blockIdx.x: pass 0: dots V_i . w -> hcol; pass 1: w -= sum hcol_i V_i, dots
 // -> hcol2; pass 2: w -= sum hcol2_i V_i, ||w||^2 -> nrm2, then the Givens
 // update of the column.  The last CTA of a column sums its partials.
-// Arithmetic: the basis precision T for the update and for each lane's
-// partial dot product (an FP32 basis is good to 6e-8 and a lane sums about
-// 20 terms; FP64 arithmetic is 64 times slower on this GPU), FP64 from the
-// lane sums on; the FP64 basis of the plain FP64 solve stays FP64 throughout.
-template <typename T>
+// Arithmetic A of the update and of each lane's partial dot product: FP64
+// (the method's orthogonalisation), or the FP32 basis's own precision under
+// the fast refinement option (an FP32 basis is good to 6e-8 and a lane sums
+// about 20 terms; FP64 arithmetic is 64 times slower on this GPU); FP64 from
+// the lane sums on in both.
+template <typename T, typename A>
 __global__ void k_gs_step(const T* __restrict__ V, T* __restrict__ w, int pass, GState s, StepArgs a) {
   __shared__ double sh[32];
-  __shared__ T cf[kMaxRestart + 1];
+  __shared__ A cf[kMaxRestart + 1];
   const int col = blockIdx.y;
   const int chunk = blockIdx.x;
   if (!s.active[col]) return;                        // whole column: no CTA takes a ticket
@@ -321,12 +322,12 @@ __global__ void k_gs_step(const T* __restrict__ V, T* __restrict__ w, int pass, 
   const int64_t vstride = (int64_t)a.nrhs * N;
   if (pass > 0) {
     const double* coef = (pass == 1 ? s.hcol : s.hcol2) + (int64_t)col * (a.m + 1);
-    for (int i = threadIdx.x; i < nv; i += blockDim.x) cf[i] = (T)coef[i];
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) cf[i] = (A)coef[i];
     __syncthreads();
     for (int64_t p = lo + threadIdx.x; p < hi; p += blockDim.x) {
-      T acc = wc[p];
-      for (int i = 0; i < nv; ++i) acc -= cf[i] * V[i * vstride + (int64_t)col * N + p];
-      wc[p] = acc;
+      A acc = (A)wc[p];
+      for (int i = 0; i < nv; ++i) acc -= cf[i] * (A)V[i * vstride + (int64_t)col * N + p];
+      wc[p] = (T)acc;
     }
     __syncthreads();
   }
@@ -335,8 +336,8 @@ __global__ void k_gs_step(const T* __restrict__ V, T* __restrict__ w, int pass, 
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int i = wid; i < nd; i += nw) {
     const T* vi = dot ? V + i * vstride + (int64_t)col * N : wc;
-    T lacc = 0;
-    for (int64_t p = lo + lane; p < hi; p += 32) lacc += vi[p] * wc[p];
+    A lacc = 0;
+    for (int64_t p = lo + lane; p < hi; p += 32) lacc += (A)vi[p] * (A)wc[p];
     double acc = (double)lacc;
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if (lane == 0) a.partial[((int64_t)col * a.part_ld + i) * a.nchunks + chunk] = acc;
@@ -456,10 +457,13 @@ static int gmres(Handle& h, const T* r, T* d, int nrhs, const double* rtol_host,
   VC_TRY(mvm_prepare(h, nrhs, sizeof(C_t<T>)));
 
   // ---- the restart-cycle graph, built once per key ----
-  const uintptr_t key[10] = {sizeof(T), (uintptr_t)adjoint, (uintptr_t)nrhs, (uintptr_t)N, (uintptr_t)m,
+  const bool fastgs = sizeof(T) == 4 && h.opts.fast_refine != 0;
+  const uintptr_t key[10] = {sizeof(T) + (fastgs ? 16 : 0), (uintptr_t)adjoint, (uintptr_t)nrhs, (uintptr_t)N,
+                             (uintptr_t)m,
                              (uintptr_t)h.solver_ws.p, (uintptr_t)h.ws.p,
-                             (uintptr_t)(h.path + 2) | ((uintptr_t)(h.yvar[0] + 2 * h.yvar[1] + 4 * h.zfvar) << 8) | ((uintptr_t)h.zvar << 16) |
-                                 ((uintptr_t)(h.ztx + 2) << 24),
+                             (uintptr_t)(h.path + 2) |
+                                 ((uintptr_t)(h.yvar[0] + 2 * h.yvar[1] + 4 * h.zfvar) << 8) |
+                                 ((uintptr_t)h.zvar << 16) | ((uintptr_t)(h.ztx + 2) << 24),
                              (uintptr_t)(h.ytx[0] + 2) | ((uintptr_t)(h.ytx[1] + 2) << 8), (uintptr_t)h.act_map.d};
   bool same = h.gm.exec != nullptr;
   for (int i = 0; same && i < 10; ++i) same = h.gm.key[i] == key[i];
@@ -500,9 +504,15 @@ static int gmres(Handle& h, const T* r, T* d, int nrhs, const double* rtol_host,
         sa.N = N; sa.nrhs = nrhs; sa.m = m; sa.nchunks = nch; sa.part_ld = m + 1;
         sa.ctl = ctl; sa.rtol = rtol; sa.jdev = jdev; sa.partial = partial;
         sa.tickets = tickets; sa.invn = invn;
-        k_gs_step<T><<<gsw, kDotTB, 0, cap>>>(V, W2, 0, s, sa);
-        k_gs_step<T><<<gsw, kDotTB, 0, cap>>>(V, W2, 1, s, sa);
-        k_gs_step<T><<<gsw, kDotTB, 0, cap>>>(V, W2, 2, s, sa);
+        if (fastgs) {
+          k_gs_step<T, T><<<gsw, kDotTB, 0, cap>>>(V, W2, 0, s, sa);
+          k_gs_step<T, T><<<gsw, kDotTB, 0, cap>>>(V, W2, 1, s, sa);
+          k_gs_step<T, T><<<gsw, kDotTB, 0, cap>>>(V, W2, 2, s, sa);
+        } else {
+          k_gs_step<T, double><<<gsw, kDotTB, 0, cap>>>(V, W2, 0, s, sa);
+          k_gs_step<T, double><<<gsw, kDotTB, 0, cap>>>(V, W2, 1, s, sa);
+          k_gs_step<T, double><<<gsw, kDotTB, 0, cap>>>(V, W2, 2, s, sa);
+        }
         k_store_next<T><<<gN, TB, 0, cap>>>(W2, V, vcur, s, sa, tickets + nrhs, h.act_map.d);
         k_loop_cond<<<1, 32, 0, cap>>>(hc, ctl, jdev, s.active, nrhs, m);
       }
@@ -634,9 +644,9 @@ int solve(Handle& h, const double* B, int nrhs, double tol, double* X, voxcap_st
   double worst = 0.0;
   bool conv = false;
   int sweeps = 0;
-  // Under refinement the residual of a column whose last sweep only had to
-  // reach a large residual (expected relative residual >= 1e-5) is formed
-  // with an FP32 product: its error (~1e-7 of |b|) is two orders below that
+  // Under refinement with the fast option, the residual of a column whose
+  // last sweep only had to reach a large residual (expected relative residual
+  // >= 1e-5) is formed with an FP32 product: its error (~1e-7 of |b|) is two orders below that
   // residual, so the next correction is as good as with an FP64 residual.
   // Convergence is only ever decided on an FP64 residual, and each column's
   // choice depends on its own history only (products are column by column).
@@ -699,7 +709,7 @@ int solve(Handle& h, const double* B, int nrhs, double tol, double* X, voxcap_st
     ++sweeps;
     for (int c = 0; c < nrhs; ++c) {
       const double rel = bn[c] > 0.0 ? rn[c] / bn[c] : 0.0;
-      use32[c] = refine && f[c] != 0.0 && rel * itol[c] >= 1e-5;
+      use32[c] = refine && h.opts.fast_refine && f[c] != 0.0 && rel * itol[c] >= 1e-5;
     }
     int left = std::max(1, h.opts.max_iters - cnt.iters);
     VC_CUDA(cudaMemcpyAsync(fac.p, f.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));

@@ -43,7 +43,8 @@ class Opts(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("max_iters", ctypes.c_int),
                 ("max_sweeps", ctypes.c_int), ("nv", ctypes.c_int * 3),
                 ("precond", ctypes.c_int), ("pad_mode", ctypes.c_int),
-                ("entries", ctypes.c_int), ("tucker", ctypes.POINTER(Tucker))]
+                ("entries", ctypes.c_int), ("tucker", ctypes.POINTER(Tucker)),
+                ("fast_refine", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

@@ -367,12 +367,15 @@ def test_preconditioner_matches_dense(kind, nv, bar64):
         assert rel_l2(z32[c], R @ r[c]) < 1e-5
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine", "fp32_refine_fast"])
 @pytest.mark.parametrize("w", [SMALL[0], SMALL[1], SMALL[3], SMALL[4]], ids=lambda w: w.name)
 def test_capacitance_matches_oracle(w, precision):
+    """fp32_refine_fast: the fast refinement option (FP32 Gram-Schmidt
+    arithmetic, FP32 residuals for early sweeps) meets the same bars."""
     ps, A = dense(w)
     Cref, _, _ = O.capacitance(ps, A=A, voxel_size=w.voxel_size)
-    vc = make(w, precision=precision)
+    fast = precision.endswith("_fast")
+    vc = make(w, precision=precision.replace("_fast", ""), fast_refine=int(fast))
     C, st = vc.capacitance(tol=1e-8)
     assert st["converged"] == 1
     err = np.abs(C - Cref) / np.abs(Cref).max()
@@ -387,8 +390,8 @@ def test_solve_residual_and_dense_solution():
     rng = np.random.default_rng(2)
     B = rng.standard_normal((2, ps.n))
     Xref = np.linalg.solve(A, B.T).T
-    for precision in ("fp64", "fp32_refine"):
-        vc = make(w, precision=precision)
+    for precision, fast in (("fp64", 0), ("fp32_refine", 0), ("fp32_refine", 1)):
+        vc = make(w, precision=precision, fast_refine=fast)
         X, st = vc.solve(torch.tensor(B, device="cuda"), tol=1e-10)
         X = X.cpu().numpy()
         for c in range(2):
