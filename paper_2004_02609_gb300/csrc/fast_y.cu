@@ -81,18 +81,18 @@ __global__ void __launch_bounds__(NT) k_ypass_fast(Geom g, int G, const C* __res
       });
 }
 
-template <bool INV, int R1, int R2, int R3, int TX, int NT>
-__global__ void __launch_bounds__(NT) k_ypass_pipe(Geom g, int G, const C* __restrict__ in, C* __restrict__ out,
+template <bool INV, int R1, int R2, int R3, int TX, int NT, typename CT = C>
+__global__ void __launch_bounds__(NT) k_ypass_pipe(Geom g, int G, const CT* __restrict__ in, CT* __restrict__ out,
                                                    int64_t in_bstride, int64_t out_bstride,
-                                                   const C* __restrict__ stw, int twn, int off2, int off3,
-                                                   const C* __restrict__ phy, int ntile, int nitems) {
+                                                   const CT* __restrict__ stw, int twn, int off2, int off3,
+                                                   const CT* __restrict__ phy, int ntile, int nitems) {
   using P = fast::Plan<R1, R2, R3>;
   constexpr int L = P::L;
   static_assert(NT % TX == 0, "a thread keeps one line of the tile in every stage");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* bufs = reinterpret_cast<C*>(smem_raw);     // [2][L][TX]
-  C* tws = bufs + 2 * L * TX;
-  C* phs = tws + twn;                           // half-voxel phases of the y grid
+  CT* bufs = reinterpret_cast<CT*>(smem_raw);   // [2][L][TX]
+  CT* tws = bufs + 2 * L * TX;
+  CT* phs = tws + twn;                          // half-voxel phases of the y grid
   fast::load_table<NT>(tws, stw, twn);
   fast::load_table<NT>(phs, phy, L);
   const int H = g.Hx;
@@ -110,19 +110,20 @@ __global__ void __launch_bounds__(NT) k_ypass_pipe(Geom g, int G, const C* __res
     const int z = (int)(q / H), kx = (int)(q - (int64_t)z * H);
     return (int64_t)b * bstride + ((int64_t)grid * g.Lz + z) * ((int64_t)len * H) + kx;
   };
-  auto prefetch = [&](int item, C* buf) {
+  auto prefetch = [&](int item, CT* buf) {
     int grid;
     const int64_t o = line_of(item, in_bstride, Lin, grid);
     if (o >= 0) {
-      const C* src = in + o;
-      for (int y = (int)threadIdx.x / TX; y < Lin; y += NT / TX) fast::cp_async8(&buf[y * TX + c], src + (int64_t)y * H);
+      const CT* src = in + o;
+      for (int y = (int)threadIdx.x / TX; y < Lin; y += NT / TX)
+        fast::cp_async_elem(&buf[y * TX + c], src + (int64_t)y * H);
     }
     fast::cp_async_commit();
   };
   int cur = 0;
   if ((int)blockIdx.x < nitems) prefetch(blockIdx.x, bufs);
   for (int item = blockIdx.x; item < nitems; item += gridDim.x, cur ^= 1) {
-    C* buf = bufs + cur * L * TX;
+    CT* buf = bufs + cur * L * TX;
     fast::cp_async_wait_all();
     __syncthreads();                 // this tile's rows are in; the other buffer is free
     if (item + (int)gridDim.x < nitems) prefetch(item + gridDim.x, bufs + (cur ^ 1) * L * TX);
@@ -132,8 +133,8 @@ __global__ void __launch_bounds__(NT) k_ypass_pipe(Geom g, int G, const C* __res
     // first stage in place: rows >= Lin are the zero padding (the forward
     // pass reads only the lower half of its butterflies' inputs)
     fast::stage_inplace_ld<L, R1, 1, TX, NT, INV, TX, INV ? R1 : R1 / 2>(
-        buf, tws, [&](int cc, int y) -> C {
-          C v = mk<C>(0.f, 0.f);
+        buf, tws, [&](int cc, int y) -> CT {
+          CT v = mk<CT>(0, 0);
           if (y < Lin) {
             v = buf[y * TX + cc];
             if (INV && phase) v = cmul(v, cconj(phs[y]));
@@ -142,10 +143,10 @@ __global__ void __launch_bounds__(NT) k_ypass_pipe(Geom g, int G, const C* __res
         });
     if constexpr (P::NST == 3) fast::stage_inplace<L, R2, R1, TX, NT, INV>(buf, tws + off2);
     // last stage: buffer -> registers -> HBM
-    C* dst = out + (oo >= 0 ? oo : 0);
+    CT* dst = out + (oo >= 0 ? oo : 0);
     fast::stage<L, P::RL, P::NSL, TX, NT, INV, P::RL, INV ? (P::RL + 1) / 2 : P::RL>(
-        tws + (P::NST == 3 ? off3 : off2), [&](int cc, int pos) -> C { return buf[pos * TX + cc]; },
-        [&](int, int y, C v) {
+        tws + (P::NST == 3 ? off3 : off2), [&](int cc, int pos) -> CT { return buf[pos * TX + cc]; },
+        [&](int, int y, CT v) {
           if (oo >= 0 && y < Lout) {
             if (!INV && phase) v = cmul(v, phs[y]);
             dst[(int64_t)y * H] = v;
@@ -155,13 +156,15 @@ __global__ void __launch_bounds__(NT) k_ypass_pipe(Geom g, int G, const C* __res
   fast::cp_async_wait_all();
 }
 
-template <bool INV, int R1, int R2, int R3, int TX, int NT>
-int launch_ypipe(const Handle& h, int G, const C* in, C* out, int64_t ibs, int64_t obs, int B, cudaStream_t st) {
+template <bool INV, int R1, int R2, int R3, int TX, int NT, typename CT = C>
+int launch_ypipe(const Handle& h, int G, const CT* in, CT* out, int64_t ibs, int64_t obs, int B, cudaStream_t st) {
   const Geom& g = h.g;
-  const Plan1D<float2>& p = h.pf[1];
+  constexpr bool F64 = sizeof(CT) == 16;
+  const Plan1D<CT>& p = *reinterpret_cast<const Plan1D<CT>*>(F64 ? (const void*)&h.pd[1] : (const void*)&h.pf[1]);
+  const CT* phy = reinterpret_cast<const CT*>(F64 ? (const void*)h.phd[1] : (const void*)h.phf[1]);
   constexpr int L = R1 * R2 * R3;
-  const size_t sm = ((size_t)2 * L * TX + p.twn + L) * sizeof(C);
-  auto kern = k_ypass_pipe<INV, R1, R2, R3, TX, NT>;
+  const size_t sm = ((size_t)2 * L * TX + p.twn + L) * sizeof(CT);
+  auto kern = k_ypass_pipe<INV, R1, R2, R3, TX, NT, CT>;
   VC_TRY(set_smem(kern, sm));
   VC_CHECK(2 * g.Ly <= L, VOXCAP_ERR_UNSUPPORTED, "y padding shorter than twice the grid");
   const int64_t ntile = ((int64_t)g.Lz * g.Hx + TX - 1) / TX;
@@ -172,8 +175,8 @@ int launch_ypipe(const Handle& h, int G, const C* in, C* out, int64_t ibs, int64
   VC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h.device));
   VC_CHECK(per_sm > 0, VOXCAP_ERR_UNSUPPORTED, "the persistent y pass does not fit an SM");
   const int grid = (int)std::min<int64_t>(items, (int64_t)per_sm * sms);
-  kern<<<grid, NT, sm, st>>>(g, G, in, out, ibs, obs, p.stw, p.twn, p.twoff[1], p.nst >= 3 ? p.twoff[2] : 0,
-                             h.phf[1], (int)ntile, (int)items);
+  kern<<<grid, NT, sm, st>>>(g, G, in, out, ibs, obs, p.stw, p.twn, p.twoff[1], p.nst >= 3 ? p.twoff[2] : 0, phy,
+                             (int)ntile, (int)items);
   ::vc::note_launch();
   VC_CUDA(cudaGetLastError());
   return VOXCAP_OK;
@@ -223,7 +226,33 @@ int dispatch_y(const Handle& h, int G, const C* in, C* out, int64_t ibs, int64_t
   return VOXCAP_ERR_UNSUPPORTED;
 }
 
+// FP64: the persistent pass, tile widths for about 74 KB per line buffer
+template <bool INV>
+int dispatch_y64(const Handle& h, int G, const double2* in, double2* out, int64_t ibs, int64_t obs, int B,
+                 cudaStream_t st) {
+  const Plan1D<double2>& p = h.pd[1];
+  const int* r = p.radix;
+  using D = double2;
+  if (p.nst == 2) {
+    if (r[0] == 4 && r[1] == 9) return launch_ypipe<INV, 4, 9, 1, 16, 144, D>(h, G, in, out, ibs, obs, B, st);
+    if (r[0] == 8 && r[1] == 9) return launch_ypipe<INV, 8, 9, 1, 16, 144, D>(h, G, in, out, ibs, obs, B, st);
+    if (r[0] == 16 && r[1] == 9) return launch_ypipe<INV, 16, 9, 1, 16, 144, D>(h, G, in, out, ibs, obs, B, st);
+  } else if (p.nst == 3 && r[2] == 9) {
+    if (r[0] == 8 && r[1] == 4) return launch_ypipe<INV, 8, 4, 9, 8, 288, D>(h, G, in, out, ibs, obs, B, st);
+    if (r[0] == 16 && r[1] == 4) return launch_ypipe<INV, 16, 4, 9, 4, 144, D>(h, G, in, out, ibs, obs, B, st);
+    if (r[0] == 16 && r[1] == 8) return launch_ypipe<INV, 16, 8, 9, 4, 288, D>(h, G, in, out, ibs, obs, B, st);
+  }
+  set_error("no compiled y-pass plan for this length");
+  return VOXCAP_ERR_UNSUPPORTED;
+}
+
 }  // namespace
+
+int fast_ypass_f64(const Handle& h, bool inv, int G, const double2* in, double2* out, int64_t in_bstride,
+                   int64_t out_bstride, int B, cudaStream_t st) {
+  if (inv) return dispatch_y64<true>(h, G, in, out, in_bstride, out_bstride, B, st);
+  return dispatch_y64<false>(h, G, in, out, in_bstride, out_bstride, B, st);
+}
 
 bool fast_plan_ok(const Plan1D<float2>& p) {
   const int* r = p.radix;

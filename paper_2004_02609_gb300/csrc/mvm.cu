@@ -321,6 +321,9 @@ int mvm(Handle& h, const T* x, T* y, int nrhs, bool adjoint, T* field_out, void*
     VC_CUDA(cudaGetLastError());
   }
   const bool fast_y = std::is_same<T, float>::value && h.path == 1 && fast_plan_ok(h.pf[1]);
+  // FP64 products: the persistent compiled y passes wherever the plan has one
+  // (the generic FP64 passes fit only 2 lines of the longest plans in a CTA)
+  const bool fast_y64 = std::is_same<T, double>::value && fast_plan_ok(h.pf[1]);
   const bool fast_z = std::is_same<T, float>::value && h.path == 1 && !adjoint && fast_z_ok(h);
   // yfwd: bufX [B][GI] -> bufY [B][6] (first GI grids)
   // y tiles: the tuned widths for FP32 (4..16 columns), else the widest that fits
@@ -331,6 +334,9 @@ int mvm(Handle& h, const T* x, T* y, int nrhs, bool adjoint, T* field_out, void*
   if (fast_y) {
     VC_TRY(fast_ypass(h, false, GI, reinterpret_cast<const float2*>(bufX), reinterpret_cast<float2*>(bufY),
                       (int64_t)GI * gX, (int64_t)6 * gY, B, h.yvar[0], st));
+  } else if (fast_y64) {
+    VC_TRY(fast_ypass_f64(h, false, GI, reinterpret_cast<const double2*>(bufX), reinterpret_cast<double2*>(bufY),
+                          (int64_t)GI * gX, (int64_t)6 * gY, B, st));
   } else {
     const int TXy = TXf;
     const int TBy = TXy >= 16 ? 256 : 128;
@@ -353,6 +359,9 @@ int mvm(Handle& h, const T* x, T* y, int nrhs, bool adjoint, T* field_out, void*
   if (fast_y) {
     VC_TRY(fast_ypass(h, true, GO, reinterpret_cast<const float2*>(bufY), reinterpret_cast<float2*>(bufX),
                       (int64_t)6 * gY, (int64_t)GO * gX, B, h.yvar[1], st));
+  } else if (fast_y64) {
+    VC_TRY(fast_ypass_f64(h, true, GO, reinterpret_cast<const double2*>(bufY), reinterpret_cast<double2*>(bufX),
+                          (int64_t)6 * gY, (int64_t)GO * gX, B, st));
   } else {
     const int TXy = TXi;
     const int TBy = TXy >= 16 ? 256 : 128;

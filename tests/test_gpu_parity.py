@@ -276,7 +276,8 @@ def test_matvec_compiled_plans(n, axis):
     """The compiled-plan FP32 passes (path 1) on every compiled length (x and
     y: 36, 72, 144, 288, 576, 1152 with two or three radix stages; z: 36, 72,
     144), forward (compiled x, y and z passes) and transposed (compiled y
-    passes),
+    passes), in every launch variant, and the FP64 products (compiled y
+    passes) at 1e-12,
     against the dense oracle; and the generic passes (path 0) on the same
     handle.  The full padded transforms run although the structure is small."""
     import torch
@@ -298,6 +299,13 @@ def test_matvec_compiled_plans(n, axis):
             assert rel_l2(t[r], A.T @ X[r]) < 2e-6, (path, r)
     # the variants differ in tiling only: same arithmetic per line, same bits
     assert np.array_equal(res[1][0], res[15][0]) and np.array_equal(res[1][1], res[15][1])
+    # FP64 products: the compiled y passes on these lengths
+    x64 = torch.tensor(X, device="cuda", dtype=torch.float64)
+    f = vc.matvec(x64).cpu().numpy()
+    t = vc.matvec(x64, adjoint=True).cpu().numpy()
+    for r in range(2):
+        assert rel_l2(f[r], A @ X[r]) < 1e-12, ("fp64", r)
+        assert rel_l2(t[r], A.T @ X[r]) < 1e-12, ("fp64", r)
     p = vc.set_product_path(-1)
     assert p == 0 or (p & 1 and p < 16)
 
