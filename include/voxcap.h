@@ -410,9 +410,11 @@ int voxcap_setup_times(const voxcap_t* h, double* seconds);
 
 /*
  * voxcap_set_product_path -- which kernels run the handle's FP32 products
- * (Eqs. 9-12; an implementation choice, same results to rounding):
- *  path 0   the generic passes (any padded length; the FP64 products always
- *           use them);
+ * (Eqs. 9-12; an implementation choice, same results to rounding).  The
+ * FP64 products do not depend on it: they use the compiled persistent y
+ * passes wherever the y length has a compiled plan and the generic passes
+ * otherwise.
+ *  path 0   the generic passes (any padded length);
  *  path 1   passes compiled for fixed radix plans wherever the padded length
  *           of an axis has one (x and y: 36, 72, 144, 288, 576, 1152; z: 36,
  *           72, 144; forward z pass only), the generic passes elsewhere, each
