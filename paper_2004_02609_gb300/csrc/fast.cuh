@@ -1,11 +1,11 @@
 // Compile-time Stockham stages for the products on the common padded
-// lengths (2^a and 2^a * 9 with two or three radix stages): the length, the
-// radices, the tile width and the thread count are template parameters, so
-// every index of a stage is constant-folded, and a tile needs one shared-
-// memory buffer (a middle stage runs in place: each thread holds all of its
-// butterflies in registers across a barrier).  Used by the passes in
-// fast_{x,y,z}.cu; the generic passes in mvm.cu / zmac.cuh cover every other
-// length and the FP64 products.
+// lengths (2^a * 9 with two or three radix stages): the length, the radices,
+// the tile width and the thread count are template parameters, so every
+// index of a stage is constant-folded, and a tile needs one shared-memory
+// buffer (a middle stage runs in place: each thread holds all of its
+// butterflies in registers across a barrier).  Used by the FP32 passes in
+// fast_{x,y,z}.cu and by the FP64 y passes; the generic passes in mvm.cu /
+// zmac.cuh cover every other length and the FP64 x and z passes.
 #pragma once
 #include "internal.h"
 

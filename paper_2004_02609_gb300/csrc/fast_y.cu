@@ -1,4 +1,4 @@
-// y passes of the FP32 products (Eqs. 9-11) on compiled plans: the forward
+// y passes of the products (Eqs. 9-11) on compiled plans: the forward
 // transform along y of the x-transformed charge planes (zero rows y >= N_y+1
 // are the padding and are not read) and the inverse transform back to the
 // N_y+1 rows the panels need, with the half-voxel phase of the y grids.
@@ -17,7 +17,8 @@
 // line buffers; at the start of a tile it issues the cp.async copies of the
 // next tile's rows into the other buffer, so that the HBM reads of one tile
 // overlap the transform of the previous one, and every stage runs in place
-// on shared memory (the last one writes HBM).
+// on shared memory (the last one writes HBM).  It is also instantiated for
+// double2: the y passes of the FP64 products.
 #include <algorithm>
 
 #include "fast.cuh"

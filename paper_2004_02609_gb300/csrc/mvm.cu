@@ -20,8 +20,11 @@
 //         gather at the panels
 // The transposed product runs the same passes with the panel values split
 // by row kind (6 input grids), the conjugated kernels and 3 output grids.
-// The z pass lives in zmac.cuh (one translation unit per precision and
-// direction); its variant and the y passes' tile widths are tuned at set-up.
+// The generic z pass lives in zmac.cuh (one translation unit per precision
+// and direction).  FP32 products on the compiled lengths run the passes of
+// fast_{x,y,z}.cu instead (path 1 and its launch variants, tuned at set-up
+// against the generic passes' radix orders and tile widths); FP64 products
+// run the compiled y passes there and the generic x and z passes.
 #include <type_traits>
 
 #include "fast.cuh"
