@@ -19,7 +19,10 @@ each function citing the passage it follows (arxiv 2004.02609):
 * ``precond_apply``  -- block-diagonal-diagonal preconditioner of Eq. 14
                         (Sec. II.D) and the conventional variants used for
                         comparison in Sec. III.A.
-* ``capacitance_grad`` -- dC/d(eps) by a dense adjoint solve.
+* ``capacitance_grad`` -- dC/d(eps) by a dense adjoint solve, with the
+                        limit of Eq. 7 for faces between equal
+                        permittivities (``equal_eps_faces``), which carry
+                        no panel but gain one as soon as a side changes.
 * ``tucker_hosvd`` / ``tucker_expand`` -- Eq. 13 (truncated HOSVD, einsum).
 * ``fft_gmres``      -- (module) the FFT-accelerated product of Eqs. 9-11 by
                         directly evaluated circulant kernels and scipy FFTs,
@@ -406,9 +409,18 @@ def capacitance_grad(labels, conductor_id, eps_r, dL_dC, voxel_size: float = 1.0
     C_ij = eps0 dv * w_i^T rho_j, A rho_j = b_j (Eqs. 4, 8).  Only I' on the
     dielectric rows (Eq. 7) and the free-charge factors w depend on eps, so
       dL/dth = eps0 dv * sum_ij G_ij [ (dw_i/dth)^T rho_j - lam_i^T (dA/dth) rho_j ],
-    with A^T lam_i = w_i.  Panels whose two sides have equal permittivity do
-    not exist in this dense system; a label whose voxels are all interior to a
-    uniform region therefore only sees its boundary panels.
+    with A^T lam_i = w_i.
+
+    A face between two non-conductors of equal permittivity eps carries no
+    panel, but it becomes one as soon as either side changes: with eps_a =
+    eps + d its I' = (2 eps + d) / (2 d) is large, the new panel's charge is
+    -(r^T rho_j) / I' to first order (r: the E' row of the face against the
+    existing panels, so r^T rho_j is the normal field there), and through the
+    column c of the new panel (P' on conductor rows, E' on dielectric rows)
+    C_ij changes by eps0 dv (lam_i^T c)(r^T rho_j) d / eps.  So such a face adds
+    +eps0 dv (c^T lam_i)(r^T rho_j) / eps to dC_ij/d(eps_a) and the negative
+    of that to dC_ij/d(eps_b) (Eq. 7 in the limit of equal sides; vacuum
+    outside the box is a fixed eps = 1).
     Returns (grad [n_labels], C [m x m] farads).
     """
     ps = panels(labels, conductor_id, eps_r)
@@ -443,8 +455,53 @@ def capacitance_grad(labels, conductor_id, eps_r, dL_dC, voxel_size: float = 1.0
             grad[la] -= scale * dIa * t
         if lb >= 0:
             grad[lb] -= scale * dIb * t
+    # faces without a panel between equal permittivities (the limit above)
+    ef = equal_eps_faces(labels, conductor_id, eps_r)
+    if len(ef["orient"]):
+        c2p = np.rint(2.0 * ps.centers).astype(np.int64)
+        for f in range(len(ef["orient"])):
+            of, cf = int(ef["orient"][f]), ef["center"][f]
+            d = (np.rint(2.0 * cf).astype(np.int64) - c2p) / 2.0        # face minus panels
+            r = entries(1, of, ps.orient, d, rtol=rtol)                   # E'(face <- panel l)
+            c = entries(ps.kind, ps.orient, of, -d, rtol=rtol)            # A(panel k <- face)
+            t = float((r @ X) @ (c @ Mu))
+            e = float(ef["eps"][f])
+            la, lb = int(ef["label_a"][f]), int(ef["label_b"][f])
+            if la >= 0:
+                grad[la] += scale * t / e
+            if lb >= 0:
+                grad[lb] -= scale * t / e
     C = scale * (W.T @ X)
     return grad, C
+
+
+def equal_eps_faces(labels, conductor_id, eps_r) -> dict:
+    """Faces between two non-conductor voxels (or a voxel and the vacuum
+    outside the box) of equal permittivity: they carry no panel (Sec. II.A).
+    Returns orient, face index, labels of the -axis (a) and +axis (b) sides
+    (-1 outside), the common eps and the face centres."""
+    labels = np.asarray(labels)
+    nz, ny, nx = labels.shape
+    cid = np.asarray(conductor_id, dtype=np.int64)[labels]
+    eps = np.asarray(eps_r, dtype=np.float64)[labels]
+    lab = labels.astype(np.int64)
+    out = {k: [] for k in ("orient", "face", "label_a", "label_b", "eps")}
+    for o in range(3):
+        ca, cb = _sides(cid, o, -1)
+        ea, eb = _sides(eps, o, 1.0)
+        la, lb = _sides(lab, o, -1)
+        ca, cb, ea, eb, la, lb = (x.reshape(-1) for x in (ca, cb, ea, eb, la, lb))
+        idx = np.nonzero((ca < 0) & (cb < 0) & (ea == eb) & ((la >= 0) | (lb >= 0)))[0]
+        out["orient"].append(np.full(len(idx), o, np.int8))
+        out["face"].append(idx.astype(np.int64))
+        out["label_a"].append(la[idx])
+        out["label_b"].append(lb[idx])
+        out["eps"].append(ea[idx])
+    out = {k: np.concatenate(v) for k, v in out.items()}
+    tmp = PanelSet(nx, ny, nz, out["orient"], out["face"], np.zeros(len(out["face"]), np.int8),
+                   np.zeros(0), np.zeros(0), np.zeros(0), np.zeros(0), np.zeros(0), 0, centers=np.zeros((0, 3)))
+    out["center"] = panel_centers(tmp)
+    return out
 
 
 # --------------------------------------------------------------------------

@@ -44,7 +44,9 @@ def test_gradient_matches_dense_adjoint(precision):
 
 def test_gradient_equal_permittivity_faces_by_finite_differences():
     """Faces whose two sides have equal eps carry no panel; their voxels still
-    have a gradient (a panel appears as soon as one side changes)."""
+    have a gradient (a panel appears as soon as one side changes): against the
+    oracle's dense adjoint, which adds the equal-sides limit of Eq. 7 for
+    those faces, at every voxel, and against central differences."""
     import torch
     from paper_2004_02609_gb300 import voxcap as V
     lab, cid, eps = _tiny(1, (6, 5, 4))
@@ -54,6 +56,9 @@ def test_gradient_equal_permittivity_faces_by_finite_differences():
     vc = V.VoxCap(lab, cid, eps, 1e-6, precision="fp64", nv=4)
     vc.capacitance(tol=1e-12)
     g, _ = vc.capacitance_grad(G, tol=1e-12)
+    gref, _ = O.capacitance_grad(lab, cid, eps, G, voxel_size=1e-6, rtol=1e-12)
+    bad = np.abs(g - gref) > 1e-3 * np.abs(gref) + 1e-6 * np.max(np.abs(gref))
+    assert not np.any(bad), (np.nonzero(bad)[0][:8], g[bad][:8], gref[bad][:8])
     rng = np.random.default_rng(2)
     picks = list(rng.choice(nv // 2, 5, replace=False)) + list(nv // 2 + rng.choice(nv - nv // 2, 3, replace=False))
     h = 1e-4

@@ -456,6 +456,55 @@ def test_oracle_gradient_matches_finite_differences():
         assert abs(fd - g[v]) < 1e-3 * abs(g).max(), (v, fd, g[v])
 
 
+def test_equal_eps_faces_hand_counted():
+    """Faces between equal permittivities carry no panel: two voxels of eps 3
+    share one such face (the interior x-face); at eps 1 all 11 faces of the
+    pair are, the 10 boundary faces included (vacuum outside); a conductor
+    side never counts."""
+    lab = np.zeros((1, 1, 2), np.int32)
+    ef = O.equal_eps_faces(lab, np.array([-1]), np.array([3.0]))
+    assert len(ef["orient"]) == 1 and ef["orient"][0] == 0 and ef["face"][0] == 1
+    assert ef["label_a"][0] == 0 and ef["label_b"][0] == 0
+    np.testing.assert_array_equal(ef["center"][0], [1.0, 0.5, 0.5])
+    ef = O.equal_eps_faces(lab, np.array([-1]), np.array([1.0]))
+    assert len(ef["orient"]) == 11
+    assert sorted(np.bincount(ef["orient"], minlength=3)) == [3, 4, 4]
+    assert np.count_nonzero((ef["label_a"] < 0) | (ef["label_b"] < 0)) == 10
+    lab2 = np.array([[[0, 1]]], np.int32)
+    ef = O.equal_eps_faces(lab2, np.array([-1, 0]), np.array([1.0, 1.0]))
+    assert len(ef["orient"]) == 5 and np.all(ef["label_a"] != 1) and np.all(ef["label_b"] != 1)
+
+
+def test_oracle_gradient_at_equal_permittivity_faces():
+    """Voxels whose faces join equal permittivities (no panel there): the
+    oracle's adjoint gradient, which adds the limit of Eq. 7 for those faces,
+    against central differences of its own capacitance (step 1e-4).  Without
+    that term the two disagree by up to several times the gradient."""
+    rng = np.random.default_rng(1)
+    nx, ny, nz = 5, 4, 3
+    nv = nx * ny * nz
+    lab = np.arange(nv, dtype=np.int32).reshape(nz, ny, nx)
+    lab[0:2, 0:2, 0:2] = nv
+    lab[1:3, 2:4, 3:5] = nv + 1
+    cid = np.full(nv + 2, -1, np.int32)
+    cid[nv], cid[nv + 1] = 0, 1
+    eps = np.concatenate([1.5 + 4 * rng.random(nv), [1.0, 1.0]])
+    eps[: nv // 2] = 3.0                      # half of the voxels share one value
+    G = np.array([[0.3, 1.0], [0.0, -0.5]])
+    g, _ = O.capacitance_grad(lab, cid, eps, G, rtol=1e-12)
+    free = [v for v in range(nv) if np.any(lab == v)]
+    picks = [v for v in free if v < nv // 2][:4] + [v for v in free if v >= nv // 2][:2]
+    h = 1e-4
+    for v in picks:
+        ep, em = eps.copy(), eps.copy()
+        ep[v] += h
+        em[v] -= h
+        Cp = O.capacitance(O.panels(lab, cid, ep), rtol=1e-12)[0]
+        Cm = O.capacitance(O.panels(lab, cid, em), rtol=1e-12)[0]
+        fd = float(np.sum(G * (Cp - Cm))) / (2 * h)
+        assert abs(fd - g[v]) <= 1e-6 * abs(fd) + 1e-9 * np.max(np.abs(g)), (v, fd, g[v])
+
+
 def test_tucker_roundtrip():
     """Eq. 13: with full ranks the restore reproduces the tensor; truncated,
     the Frobenius error stays within tol."""
